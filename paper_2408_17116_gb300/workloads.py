@@ -1,0 +1,73 @@
+"""Seeded synthetic workloads shared by the tests, the smoke check and the benchmark.
+
+This module holds geometry descriptions, parameters and seeded random draws only;
+none of the method's arithmetic lives here.  Every body is a cube-mapped
+ellipsoid (6 m^2 curvilinear patches, the patch family of the paper's sphere
+experiments, Sec. IV: 24..4056 patches = 6 m^2), wavelength 1 m (k = 2 pi).
+
+Random incidence angles use numpy's Philox counter-based generator
+(Philox4x64-10) seeded with 2408017116: theta = arccos(1 - 2U), phi = 2 pi U,
+polarisation = theta-hat.
+"""
+import numpy as np
+
+SEED = 2408017116
+WAVELENGTH = 1.0
+K0 = 2.0 * np.pi / WAVELENGTH
+
+
+def body(center=(0.0, 0.0, 0.0), semi=(0.5, 0.5, 0.5), rot=None):
+    """15 doubles: center[3], semi-axes[3], rotation[9] (row-major)."""
+    R = np.eye(3) if rot is None else np.asarray(rot, dtype=np.float64).reshape(3, 3)
+    return np.concatenate([np.asarray(center, float), np.asarray(semi, float), R.reshape(-1)])
+
+
+def incidence(nrhs, seed=SEED):
+    """nrhs seeded plane waves: (khat[nrhs,3], pol[nrhs,3])."""
+    g = np.random.Generator(np.random.Philox(seed))
+    u = g.random((nrhs, 2))
+    th = np.arccos(1.0 - 2.0 * u[:, 0])
+    ph = 2.0 * np.pi * u[:, 1]
+    kh = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+    pol = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)], 1)
+    return kh, pol
+
+
+def axial_incidence():
+    """+z propagation, x polarisation (the paper's excitation, Sec. IV.A)."""
+    return np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]])
+
+
+def rcs_cuts(nth=181):
+    """Observation directions: theta = 0..180 deg in the phi = 0 and phi = 90 deg cuts."""
+    th = np.linspace(0.0, np.pi, nth)
+    out = []
+    for ph in (0.0, 0.5 * np.pi):
+        out.append(np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1))
+    return th, np.concatenate(out, 0)
+
+
+def workload(name):
+    """Named workloads.  Sizes: N = 2 * 6 m^2 * nc^2 complex unknowns."""
+    if name == "sphere_d1_m1_nc8":  # PEC sphere, 1 wavelength diameter, 768 unknowns
+        kh, pol = axial_incidence()
+        return dict(name=name, bodies=body(semi=(0.5,) * 3)[None], ms=[1], nc=8, k=K0,
+                    leaf=64, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol, radius=0.5)
+    if name == "sphere_d8_m4_nc10":  # PEC sphere, 8 wavelengths diameter, 19,200 unknowns
+        kh, pol = incidence(4)
+        return dict(name=name, bodies=body(semi=(4.0,) * 3)[None], ms=[4], nc=10, k=K0,
+                    leaf=128, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol, radius=4.0)
+    if name == "sphere_d2_m2_nc6":  # mid-size parity case: 1,728 unknowns, ragged leaves
+        kh, pol = incidence(2, SEED + 1)
+        return dict(name=name, bodies=body(semi=(1.0,) * 3)[None], ms=[2], nc=6, k=K0,
+                    leaf=40, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol, radius=1.0)
+    if name == "ellipsoid_small":  # rotated, off-centre ellipsoid, 1,536 unknowns
+        th = 0.3
+        R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+        kh, pol = incidence(3, SEED + 2)
+        return dict(name=name, bodies=body(center=(0.1, -0.2, 0.05), semi=(1.2, 0.8, 0.5), rot=R)[None],
+                    ms=[2], nc=8, k=K0, leaf=48, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol)
+    raise KeyError(name)
+
+
+WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d2_m2_nc6", "ellipsoid_small")
