@@ -1,0 +1,178 @@
+/*
+ * hm.h -- C ABI of the GB300 (sm_103a) H-matrix accelerated CBIE direct solver.
+ *
+ * Method: arXiv 2408.17116, "H-Matrix Accelerated Direct Matrix Solver for
+ * Maxwell's Equations using the Chebyshev-based Nystrom Boundary Integral
+ * Equation Method".  The solver discretises the MFIE of a PEC body (Sec. II.A,
+ * Eq. 10, second row) with the CBIE (Sec. II.B, Eqs. 11-20), compresses the
+ * system as an H-matrix (Sec. III, Eq. 21, ACA), factors it by H-LU and solves
+ * by H-forward/back substitution (Sec. III.A, Eqs. 23-28) on the "entire matrix"
+ * ordering (Sec. III.B).
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are two IEEE doubles (re, im); "complex128" below.
+ *   - Unknowns: N = 2 * nnode.  Node n = patch * Nc^2 + kv * Nc + lu (lu: index of
+ *     the u Chebyshev node, kv: index of the v node); unknown 2n + a, a = 0 for
+ *     F^u, a = 1 for F^v (contravariant components scaled by sqrt|G|, Eq. 11).
+ *     Patch p of body b: p = offset(b) + (face * m + i) * m + j.
+ *   - Time convention exp(j w t); Green's function exp(-jkR) / (4 pi R) (Eq. 4).
+ *   - All device work is issued on the stream given to hm_create (NULL = the
+ *     legacy default stream).  Calls return after enqueuing unless stated
+ *     otherwise; hm_query, hm_farfield's host output and every "_host" getter
+ *     synchronise the stream.
+ *   - Every call returns an hm_status; on failure hm_last_error() holds a
+ *     message.  No C++ exception crosses this boundary.  One handle must not
+ *     be used from two host threads at once.
+ *   - Pointers named *_dev are device pointers owned by the caller; every other
+ *     pointer is host memory owned by the caller and is only read during the
+ *     call (inputs are copied).  The library owns all of its internal device
+ *     memory and frees it in hm_destroy.
+ */
+#ifndef HM_H
+#define HM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_handle_s *hm_handle;
+
+typedef enum {
+    HM_OK = 0,
+    HM_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad enum) */
+    HM_ERR_STATE = 2,         /* call out of order (geometry -> fill -> factor -> solve) */
+    HM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    HM_ERR_OOM = 4,           /* device allocation failed */
+    HM_ERR_SINGULAR = 5,      /* a zero pivot in a diagonal leaf of the H-LU */
+    HM_ERR_NOT_CONVERGED = 6, /* an iteration hit its limit (reported, not fatal for ACA) */
+    HM_ERR_TIMEOUT = 7,       /* a bounded device wait expired */
+    HM_ERR_NUMERIC = 8        /* NaN/Inf detected in an output */
+} hm_status;
+
+typedef enum { HM_PEC_MFIE = 0 } hm_formulation;
+typedef enum { HM_FP64 = 0 } hm_precision;
+
+/* Solver parameters.  Paper: eta and n_leaf (Sec. III, Eq. 21 and the text that
+ * follows it), ACA tolerance (Sec. IV), wavenumber from the wavelength. */
+typedef struct {
+    double k0;            /* wavenumber (rad/m) of the exterior medium */
+    int formulation;      /* hm_formulation */
+    int leaf;             /* n_leaf: clusters with at most this many unknowns are leaves */
+    double eta;           /* admissibility parameter of Eq. 21 */
+    double aca_tol;       /* ACA stopping tolerance, also the truncation tolerance */
+    double near_delta;    /* near pair: dist(bbox_q, bbox_p) < near_delta * max(diam_q, diam_p) */
+    int aca_max_rank;     /* ACA rank bound before a block is split (0 = 160) */
+    int precision;        /* hm_precision */
+    int keep_matrix;      /* nonzero: keep an unfactored copy for hm_matvec after hm_factor */
+} hm_params;
+
+/* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,
+ * c = e_f + tan(pi s/4) e1 + tan(pi t/4) e2 on each cube face (equiangular map). */
+typedef struct {
+    int family;           /* 0 = cube-mapped ellipsoid (the only family) */
+    int m;                /* patches per cube-face edge */
+    double center[3];
+    double semi_axes[3];
+    double rot[9];        /* row-major rotation */
+} hm_body;
+
+/* hm_query keys */
+enum {
+    HM_Q_N = 0,            /* number of unknowns */
+    HM_Q_NNODE = 1,
+    HM_Q_NPATCH = 2,
+    HM_Q_NEAR_PAIRS = 3,   /* near patch pairs (incl. self) */
+    HM_Q_DENSE_BLOCKS = 4,
+    HM_Q_LR_BLOCKS = 5,
+    HM_Q_CR = 6,           /* compression rate 1 - storage(H)/N^2 (Sec. IV.A) */
+    HM_Q_MAX_RANK = 7,
+    HM_Q_T_GEOMETRY = 8,   /* seconds, measured with CUDA events (last call) */
+    HM_Q_T_NEAR = 9,
+    HM_Q_T_DENSE = 10,
+    HM_Q_T_ACA = 11,
+    HM_Q_T_FACTOR = 12,
+    HM_Q_T_SOLVE = 13,
+    HM_Q_FLOPS_FACTOR = 14,/* real flops performed by the H-LU (host-side ledger) */
+    HM_Q_STORAGE = 15,     /* complex words stored by the H-matrix */
+    HM_Q_ACA_NONCONV = 16, /* admissible blocks whose ACA hit the rank bound (stored dense) */
+    HM_Q_LAUNCHES = 17,    /* kernels launched by the library since hm_create */
+    HM_Q_NEAR_QPOINTS = 18,/* kernel evaluations performed by the near-field quadrature */
+    HM_Q_MEAN_RANK = 19,
+    HM_Q_STORAGE_FACTOR = 20,/* complex words of the factored H-matrix */
+    HM_Q_T_RECOMPRESS = 21 /* seconds in the QR+SVD recompression after ACA */
+};
+
+const char *hm_version(void);
+
+/* Create a handle bound to a CUDA stream (cudaStream_t passed as void*; may be NULL)
+ * on the current device. */
+hm_status hm_create(hm_handle *h, void *cuda_stream);
+
+/* Build the discretisation: node geometry at first-kind Chebyshev nodes (Sec. II.B,
+ * Eqs. 11, 14, 17-18; Fejer weights), cluster tree and block cluster tree with the
+ * admissibility of Eq. 21 (Sec. III), near patch pairs (Eq. 20).
+ * bodies[nbodies] are copied; nodes_per_dir = Nc (2..16). */
+hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int nodes_per_dir,
+                            const hm_params *p);
+
+/* Fill the H-matrix: self/near CBIE quadrature (Eq. 20, singularity-cancelling
+ * change of variables), dense inadmissible leaves, ACA of admissible leaves and
+ * QR+SVD recompression (Sec. III).  An admissible block whose ACA reaches the rank
+ * bound min(aca_max_rank, |t||s|/(|t|+|s|)) is split into its four children and
+ * retried; on the leaf level it is stored dense. */
+hm_status hm_fill(hm_handle h);
+
+/* H-LU factorisation in place (Sec. III, Eq. 23), partial pivoting inside the
+ * diagonal dense leaves. */
+hm_status hm_factor(hm_handle h);
+
+/* Solve for nrhs plane waves E = pol exp(-jk khat.r): right-hand sides of Eq. 22
+ * (b1 = -a_v.H_inc, b2 = a_u.H_inc), H-forward substitution (Eqs. 24, 26, 27) and
+ * back substitution (Eqs. 25, 28).  inc_dirs, pols: host [nrhs][3] unit vectors.
+ * x_dev: device complex128 [nrhs][N], natural unknown order. */
+hm_status hm_solve(hm_handle h, int nrhs, const double *inc_dirs, const double *pols, void *x_dev);
+
+/* As hm_solve with host buffers: x_host receives complex128 [nrhs][N].  Copies in and
+ * out are part of the call; returns after the result is in x_host. */
+hm_status hm_solve_host(hm_handle h, int nrhs, const double *inc_dirs, const double *pols, void *x_host);
+
+/* Far field of solutions x_dev [nrhs][N] at unit directions obs_dirs (host [nang][3]):
+ * efar_dev (device complex128 [nrhs][nang][3], may be NULL) = -jk eta0/(4 pi) (I - r r)
+ * sum_j w_j (F^u a_u + F^v a_v)_j exp(jk r.r_j); rcs_host (host [nrhs][nang], may be
+ * NULL) = 4 pi |E_far|^2 in m^2.  Synchronises when rcs_host is given. */
+hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const double *obs_dirs,
+                      void *efar_dev, double *rcs_host);
+
+/* y_dev = A x_dev for nrhs vectors [nrhs][N] (natural order) with the FP64 H-matrix
+ * (available after hm_fill; after hm_factor only with keep_matrix). */
+hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev);
+
+hm_status hm_query(hm_handle h, int what, double *out);
+const char *hm_last_error(hm_handle h);
+void hm_destroy(hm_handle h);
+
+/* ---- inspection (tests and diagnostics; all synchronise) ------------------- */
+
+/* Node table, host double [nnode][14]: r[3], a_u[3], a_v[3], n[3], sqrtG, w. */
+hm_status hm_get_nodes_host(hm_handle h, double *out);
+/* Near patch pairs: host int [npairs][2] (target patch, source patch). */
+hm_status hm_get_near_pairs_host(hm_handle h, int *out);
+/* Near weights of target node tn over source patch p (must be a near pair):
+ * host complex128 [4][Nc^2], index (2b + a) * Nc^2 + j (rows b, source components a). */
+hm_status hm_get_near_block_host(hm_handle h, int tn, int p, void *out);
+/* Matrix entries A[rows[i], cols[i]] (natural unknown indices) from the fill's entry
+ * rule (near store + Nystrom far rule + identity term): host complex128 [n]. */
+hm_status hm_entries_host(hm_handle h, int n, const int *rows, const int *cols, void *out);
+/* Permutation of unknowns: perm[i] = natural index of tree-ordered unknown i (host int [N]). */
+hm_status hm_get_perm_host(hm_handle h, int *perm);
+/* Leaf blocks: host int [nblocks][6] = type (0 dense, 1 low-rank), row0, nrow, col0, ncol,
+ * rank (tree-ordered unknowns).  Pass out = NULL to get only the count in *nblocks. */
+hm_status hm_get_blocks_host(hm_handle h, int *nblocks, int *out);
+/* Dense content of leaf block b after hm_fill (dense block, or U V^H of a low-rank one):
+ * host complex128 column-major [nrow][ncol]. */
+hm_status hm_get_block_dense_host(hm_handle h, int b, void *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -1,0 +1,625 @@
+// C ABI of libhm (declared in include/hm.h).  Every entry point converts internal
+// errors to an hm_status and stores the message for hm_last_error.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hm_internal.h"
+
+#define HM_VERSION "hm-cbie-gb300 0.1 (MFIE, FP64 H-LU)"
+#define HM_DEFAULT_RANK_CAP 160
+
+void *dalloc(hm_handle_s *h, size_t bytes)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw HmError{HM_ERR_OOM, std::string("device allocation of ") + std::to_string(bytes) + " bytes failed"};
+    }
+    return p;
+}
+
+void dfree(hm_handle_s *h, void *p)
+{
+    if (p) cudaFreeAsync(p, h->stream);
+}
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a, b;
+    cudaStream_t s;
+    Timer(cudaStream_t st) : s(st)
+    {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    double stop()
+    {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return ms * 1e-3;
+    }
+};
+
+template <class F>
+hm_status guard(hm_handle h, F &&f)
+{
+    if (!h) return HM_ERR_ARG;
+    try {
+        f();
+        h->err.clear();
+        return HM_OK;
+    } catch (const HmError &e) {
+        h->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        h->err = "host allocation failed";
+        return HM_ERR_OOM;
+    } catch (...) {
+        h->err = "unknown error";
+        return HM_ERR_CUDA;
+    }
+}
+
+void free_matrix(hm_handle_s *h)
+{
+    for (Block *b : h->blocks) {
+        if (b->D) dfree(h, b->D);
+        if (b->U) dfree(h, b->U);
+        if (b->V) dfree(h, b->V);
+        if (b->piv) dfree(h, b->piv);
+        for (zc *q : b->pu) dfree(h, q);
+        for (zc *q : b->pv) dfree(h, q);
+        b->pu.clear();
+        b->pv.clear();
+        b->pk.clear();
+        b->pend_k = 0;
+        b->D = b->U = b->V = nullptr;
+        b->piv = nullptr;
+        b->k = 0;
+    }
+    free_tree(h, h->copy_blocks);
+    h->copy_root = nullptr;
+}
+
+void free_all(hm_handle_s *h)
+{
+    free_matrix(h);
+    for (Block *b : h->blocks) delete b;
+    h->blocks.clear();
+    h->leaves.clear();
+    h->root = nullptr;
+    void *ptrs[] = {h->d_bodies, h->d_patches, h->d_nodes, h->d_pair_q, h->d_pair_p, h->d_nearidx,
+                    h->d_near,   h->d_perm,    h->d_iperm};
+    for (void *p : ptrs) dfree(h, p);
+    h->d_bodies = nullptr;
+    h->d_patches = nullptr;
+    h->d_nodes = nullptr;
+    h->d_pair_q = h->d_pair_p = h->d_nearidx = nullptr;
+    h->d_near = nullptr;
+    h->d_perm = h->d_iperm = nullptr;
+}
+
+void collect_leaves(Block *b, std::vector<Block *> &out)
+{
+    if (b->type == B_HIER) {
+        for (int i = 0; i < 4; ++i) collect_leaves(b->ch[i], out);
+    } else {
+        b->leaf_id = (int)out.size();
+        out.push_back(b);
+    }
+}
+
+void rebuild_leaves(hm_handle_s *h)
+{
+    h->leaves.clear();
+    collect_leaves(h->root, h->leaves);
+}
+
+void storage(hm_handle_s *h, Block *root_unused, double &words, int &maxk, double &meank, int &ndense, int &nlr)
+{
+    (void)root_unused;
+    words = 0;
+    maxk = 0;
+    ndense = nlr = 0;
+    double ks = 0;
+    for (Block *b : h->leaves) {
+        if (b->type == B_DENSE) {
+            words += (double)b->nr * b->nc;
+            ++ndense;
+        } else {
+            words += (double)b->k * (b->nr + b->nc);
+            maxk = std::max(maxk, b->k);
+            ks += b->k;
+            ++nlr;
+        }
+    }
+    meank = nlr ? ks / nlr : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hm_version(void) { return HM_VERSION; }
+
+hm_status hm_create(hm_handle *out, void *stream)
+{
+    if (!out) return HM_ERR_ARG;
+    *out = nullptr;
+    hm_handle_s *h = new (std::nothrow) hm_handle_s();
+    if (!h) return HM_ERR_OOM;
+    h->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return HM_ERR_CUDA;
+    }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (cudaMalloc(&h->d_counter, sizeof(unsigned long long) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return HM_ERR_OOM;
+    }
+    cudaMemset(h->d_counter, 0, sizeof(unsigned long long) * 4);
+    *out = h;
+    return HM_OK;
+}
+
+hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int nodes_per_dir, const hm_params *p)
+{
+    return guard(h, [&] {
+        if (!bodies || nbodies <= 0 || !p) throw HmError{HM_ERR_ARG, "null bodies or params"};
+        if (nodes_per_dir < 2 || nodes_per_dir > HM_NC_MAX) throw HmError{HM_ERR_ARG, "nodes_per_dir out of range 2..16"};
+        if (p->formulation != HM_PEC_MFIE || p->precision != HM_FP64) throw HmError{HM_ERR_ARG, "unsupported formulation/precision"};
+        if (!(p->k0 >= 0.0) || p->leaf < 2 || !(p->eta > 0.0) || !(p->aca_tol > 0.0) || !(p->near_delta >= 0.0))
+            throw HmError{HM_ERR_ARG, "invalid parameter value"};
+        long long P = 0;
+        for (int b = 0; b < nbodies; ++b) {
+            if (bodies[b].family != 0 || bodies[b].m < 1 || bodies[b].m > 256) throw HmError{HM_ERR_ARG, "bad body"};
+            for (int d = 0; d < 3; ++d)
+                if (!(bodies[b].semi_axes[d] > 0.0)) throw HmError{HM_ERR_ARG, "semi-axes must be positive"};
+            P += 6LL * bodies[b].m * bodies[b].m;
+        }
+        if (P * nodes_per_dir * nodes_per_dir * 2 > (1LL << 30)) throw HmError{HM_ERR_ARG, "problem too large"};
+        cudaStreamSynchronize(h->stream);
+        free_all(h);
+        h->prm = *p;
+        h->tol = p->aca_tol;
+        h->nc = nodes_per_dir;
+        h->nbodies = nbodies;
+        h->bodies.clear();
+        h->patches.clear();
+        for (int b = 0; b < nbodies; ++b) {
+            DevBody B{};
+            const hm_body &hb = bodies[b];
+            for (int a = 0; a < 3; ++a) {
+                B.c[a] = hb.center[a];
+                for (int d = 0; d < 3; ++d) {
+                    B.M[3 * a + d] = hb.rot[3 * a + d] * hb.semi_axes[d];
+                    B.Minv[3 * a + d] = hb.rot[3 * d + a] / hb.semi_axes[a];
+                }
+            }
+            B.m = hb.m;
+            h->bodies.push_back(B);
+            for (int f = 0; f < 6; ++f)
+                for (int i = 0; i < hb.m; ++i)
+                    for (int j = 0; j < hb.m; ++j) h->patches.push_back(DevPatch{b, f, i, j});
+        }
+        h->npatch = (int)h->patches.size();
+        h->nnode = h->npatch * h->nc * h->nc;
+        h->N = 2 * h->nnode;
+        Timer t(h->stream);
+        plan_geometry(h);
+        h->t_geom = t.stop();
+        h->state = 1;
+    });
+}
+
+hm_status hm_fill(hm_handle h)
+{
+    return guard(h, [&] {
+        if (h->state < 1) throw HmError{HM_ERR_STATE, "hm_fill before hm_build_geometry"};
+        if (h->state > 1) {
+            free_matrix(h);
+            rebuild_block_tree(h);  // the adaptive ACA split below changes the tree
+        }
+        const int nc = h->nc, w = 2 * nc * nc;
+        // near-field quadrature (A3)
+        {
+            Timer t(h->stream);
+            if (!h->d_near) h->d_near = (zc *)dalloc(h, sizeof(zc) * (size_t)h->pair_q.size() * w * w);
+            NearRule R = h->rule;
+            std::vector<double> tab;
+            auto add_gl = [&](int q) {
+                std::vector<double> x(q), wt(q);
+                gauss_legendre_host(q, x.data(), wt.data());
+                std::vector<int> o(q);
+                for (int i = 0; i < q; ++i) o[i] = i;
+                std::sort(o.begin(), o.end(), [&](int a, int b) { return x[a] < x[b]; });
+                for (int i = 0; i < q; ++i) tab.push_back(0.5 * (x[o[i]] + 1.0));
+                for (int i = 0; i < q; ++i) tab.push_back(0.5 * wt[o[i]]);
+            };
+            add_gl(R.qd);
+            add_gl(R.qi);
+            add_gl(R.qo);
+            std::vector<double> x1d(nc);
+            cheb_nodes_host(nc, x1d.data());
+            for (int l = 0; l < nc; ++l) tab.push_back(x1d[l]);
+            // C[n][l] = alpha_n T_n(x_l) / nc  (Eq. 13)
+            std::vector<double> C(nc * nc);
+            for (int n = 0; n < nc; ++n)
+                for (int l = 0; l < nc; ++l) {
+                    double th = 3.14159265358979323846 * (2 * l + 1) / (2.0 * nc);
+                    C[n * nc + l] = (n == 0 ? 1.0 : 2.0) * std::cos(n * th) / nc;
+                }
+            double *d_tab = (double *)dalloc(h, sizeof(double) * (tab.size() + C.size()));
+            HM_CUDA(cudaMemcpyAsync(d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+            HM_CUDA(cudaMemcpyAsync(d_tab + tab.size(), C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice,
+                                    h->stream));
+            HM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), h->stream));
+            launch_near(h, d_tab, d_tab + tab.size());
+            dfree(h, d_tab);
+            h->t_near = t.stop();
+            HM_CUDA(cudaMemcpy(&h->near_points, h->d_counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        }
+        // ACA of admissible leaves (A5).  A block whose ACA reaches its rank bound is split
+        // into its four (still admissible) children and retried; at the leaf level it is
+        // stored dense.  Dense blocks therefore only occur on the leaf level.
+        {
+            Timer t(h->stream);
+            std::vector<Block *> pending;
+            for (Block *b : h->leaves)
+                if (b->type == B_LR) pending.push_back(b);
+            int cap = h->prm.aca_max_rank > 0 ? h->prm.aca_max_rank : HM_DEFAULT_RANK_CAP;
+            h->aca_nonconv = 0;
+            while (!pending.empty()) {
+                std::vector<LRDesc> descs;
+                for (Block *b : pending) {
+                    int kmax = std::min(cap, (int)((long long)b->nr * b->nc / (b->nr + b->nc)));
+                    kmax = std::max(kmax, 1);
+                    b->U = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nr * kmax);
+                    b->V = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nc * kmax);
+                    descs.push_back(LRDesc{b->r0, b->nr, b->c0, b->nc, b->U, b->V, kmax});
+                }
+                int *d_rf = (int *)dalloc(h, sizeof(int) * 2 * pending.size());
+                launch_aca(h, descs, d_rf, d_rf + pending.size());
+                std::vector<int> rf(2 * pending.size());
+                HM_CUDA(cudaMemcpyAsync(rf.data(), d_rf, sizeof(int) * rf.size(), cudaMemcpyDeviceToHost, h->stream));
+                HM_CUDA(cudaStreamSynchronize(h->stream));
+                dfree(h, d_rf);
+                std::vector<Block *> next;
+                for (size_t i = 0; i < pending.size(); ++i) {
+                    Block *b = pending[i];
+                    if (!rf[pending.size() + i]) {
+                        b->k = rf[i];
+                        continue;
+                    }
+                    ++h->aca_nonconv;
+                    dfree(h, b->U);
+                    dfree(h, b->V);
+                    b->U = b->V = nullptr;
+                    b->k = 0;
+                    const Cluster &ct = h->clusters[b->t], &cs = h->clusters[b->s];
+                    if (ct.child[0] >= 0 && cs.child[0] >= 0) {
+                        b->type = B_HIER;
+                        for (int a = 0; a < 2; ++a)
+                            for (int c = 0; c < 2; ++c) {
+                                Block *ch = new Block();
+                                h->blocks.push_back(ch);
+                                const Cluster &t2 = h->clusters[ct.child[a]], &s2 = h->clusters[cs.child[c]];
+                                ch->t = ct.child[a];
+                                ch->s = cs.child[c];
+                                ch->r0 = 2 * t2.off;
+                                ch->nr = 2 * t2.cnt;
+                                ch->c0 = 2 * s2.off;
+                                ch->nc = 2 * s2.cnt;
+                                ch->type = B_LR;
+                                b->ch[2 * a + c] = ch;
+                                next.push_back(ch);
+                            }
+                    } else {
+                        b->type = B_DENSE;
+                    }
+                }
+                pending.swap(next);
+            }
+            rebuild_leaves(h);
+            h->t_aca = t.stop();
+        }
+        // QR + SVD recompression of every low-rank leaf (A6)
+        {
+            Timer t(h->stream);
+            std::vector<Block *> keep;
+            std::vector<int> ranks;
+            for (Block *b : h->leaves)
+                if (b->type == B_LR && b->k > 0) {
+                    keep.push_back(b);
+                    ranks.push_back(b->k);
+                }
+            batched_truncate(h, keep, ranks, h->tol);
+            h->t_trunc = t.stop();
+        }
+        // dense leaves (A4)
+        {
+            Timer t(h->stream);
+            std::vector<DenseDesc> dd;
+            for (Block *b : h->leaves)
+                if (b->type == B_DENSE) {
+                    b->D = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nr * b->nc);
+                    dd.push_back(DenseDesc{b->r0, b->nr, b->c0, b->nc, b->D});
+                }
+            launch_dense_fill(h, dd);
+            h->t_dense = t.stop();
+        }
+        h->state = 2;
+    });
+}
+
+hm_status hm_factor(hm_handle h)
+{
+    return guard(h, [&] {
+        if (h->state != 2) throw HmError{HM_ERR_STATE, "hm_factor requires a filled, unfactored matrix"};
+        if (h->prm.keep_matrix) {
+            free_tree(h, h->copy_blocks);
+            h->copy_root = clone_tree(h, h->root, h->copy_blocks);
+        }
+        Timer t(h->stream);
+        h->flops_factor = 0;
+        hlu_factor(h);
+        h->t_factor = t.stop();
+        h->state = 3;
+    });
+}
+
+static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double *pol, zc *x_dev)
+{
+    if (h->state != 3) throw HmError{HM_ERR_STATE, "hm_solve requires hm_factor"};
+    if (nrhs <= 0 || !inc || !pol || !x_dev) throw HmError{HM_ERR_ARG, "bad solve arguments"};
+    std::vector<double> dirs(6 * (size_t)nrhs);
+    for (int r = 0; r < nrhs; ++r)
+        for (int d = 0; d < 3; ++d) {
+            dirs[6 * r + d] = inc[3 * r + d];
+            dirs[6 * r + 3 + d] = pol[3 * r + d];
+        }
+    Timer t(h->stream);
+    double *d_dirs = (double *)dalloc(h, sizeof(double) * dirs.size());
+    HM_CUDA(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, h->stream));
+    zc *b = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * nrhs);
+    launch_rhs(h, nrhs, d_dirs, b);
+    hsolve(h, MV{b, h->N, nrhs, h->N});
+    launch_permute(h, nrhs, b, x_dev, h->d_iperm);
+    dfree(h, b);
+    dfree(h, d_dirs);
+    h->t_solve = t.stop();  // also keeps the host vector alive until the copy is done
+}
+
+hm_status hm_solve(hm_handle h, int nrhs, const double *inc_dirs, const double *pols, void *x_dev)
+{
+    return guard(h, [&] { solve_dev(h, nrhs, inc_dirs, pols, (zc *)x_dev); });
+}
+
+hm_status hm_solve_host(hm_handle h, int nrhs, const double *inc_dirs, const double *pols, void *x_host)
+{
+    return guard(h, [&] {
+        if (!x_host) throw HmError{HM_ERR_ARG, "null x_host"};
+        zc *x = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * std::max(nrhs, 1));
+        solve_dev(h, nrhs, inc_dirs, pols, x);
+        HM_CUDA(cudaMemcpyAsync(x_host, x, sizeof(zc) * (size_t)h->N * nrhs, cudaMemcpyDeviceToHost, h->stream));
+        dfree(h, x);
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const double *obs, void *efar_dev,
+                      double *rcs_host)
+{
+    return guard(h, [&] {
+        if (h->state < 1) throw HmError{HM_ERR_STATE, "hm_farfield before hm_build_geometry"};
+        if (nrhs <= 0 || nang <= 0 || !x_dev || !obs) throw HmError{HM_ERR_ARG, "bad farfield arguments"};
+        double *d_obs = (double *)dalloc(h, sizeof(double) * 3 * nang);
+        HM_CUDA(cudaMemcpyAsync(d_obs, obs, sizeof(double) * 3 * nang, cudaMemcpyHostToDevice, h->stream));
+        double *d_rcs = rcs_host ? (double *)dalloc(h, sizeof(double) * (size_t)nrhs * nang) : nullptr;
+        launch_farfield(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
+        if (rcs_host)
+            HM_CUDA(cudaMemcpyAsync(rcs_host, d_rcs, sizeof(double) * (size_t)nrhs * nang, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        dfree(h, d_obs);
+        if (d_rcs) dfree(h, d_rcs);
+        HM_CUDA(cudaStreamSynchronize(h->stream));  // obs is only read during the call
+    });
+}
+
+hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev)
+{
+    return guard(h, [&] {
+        Block *A = nullptr;
+        if (h->state == 2)
+            A = h->root;
+        else if (h->state == 3 && h->copy_root)
+            A = h->copy_root;
+        else
+            throw HmError{HM_ERR_STATE, "hm_matvec needs a filled matrix (or keep_matrix before hm_factor)"};
+        if (nrhs <= 0 || !x_dev || !y_dev) throw HmError{HM_ERR_ARG, "bad matvec arguments"};
+        size_t n = (size_t)h->N * nrhs;
+        zc *xt = (zc *)dalloc(h, sizeof(zc) * n), *yt = (zc *)dalloc(h, sizeof(zc) * n);
+        launch_permute(h, nrhs, (const zc *)x_dev, xt, h->d_perm);
+        HM_CUDA(cudaMemsetAsync(yt, 0, sizeof(zc) * n, h->stream));
+        hmatvec(h, A, MV{xt, h->N, nrhs, h->N}, MV{yt, h->N, nrhs, h->N}, zmake(1, 0), false);
+        launch_permute(h, nrhs, yt, (zc *)y_dev, h->d_iperm);
+        dfree(h, xt);
+        dfree(h, yt);
+    });
+}
+
+hm_status hm_query(hm_handle h, int what, double *out)
+{
+    return guard(h, [&] {
+        if (!out) throw HmError{HM_ERR_ARG, "null out"};
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        double words;
+        int maxk, nd, nl;
+        double meank;
+        storage(h, h->root, words, maxk, meank, nd, nl);
+        switch (what) {
+        case HM_Q_N: *out = h->N; break;
+        case HM_Q_NNODE: *out = h->nnode; break;
+        case HM_Q_NPATCH: *out = h->npatch; break;
+        case HM_Q_NEAR_PAIRS: *out = (double)h->pair_q.size(); break;
+        case HM_Q_DENSE_BLOCKS: *out = nd; break;
+        case HM_Q_LR_BLOCKS: *out = nl; break;
+        case HM_Q_CR: *out = h->N ? 1.0 - words / ((double)h->N * h->N) : 0.0; break;
+        case HM_Q_MAX_RANK: *out = maxk; break;
+        case HM_Q_T_GEOMETRY: *out = h->t_geom; break;
+        case HM_Q_T_NEAR: *out = h->t_near; break;
+        case HM_Q_T_DENSE: *out = h->t_dense; break;
+        case HM_Q_T_ACA: *out = h->t_aca; break;
+        case HM_Q_T_RECOMPRESS: *out = h->t_trunc; break;
+        case HM_Q_T_FACTOR: *out = h->t_factor; break;
+        case HM_Q_T_SOLVE: *out = h->t_solve; break;
+        case HM_Q_FLOPS_FACTOR: *out = h->flops_factor; break;
+        case HM_Q_STORAGE: *out = words; break;
+        case HM_Q_ACA_NONCONV: *out = h->aca_nonconv; break;
+        case HM_Q_LAUNCHES: *out = (double)h->launches; break;
+        case HM_Q_NEAR_QPOINTS: *out = (double)h->near_points; break;
+        case HM_Q_MEAN_RANK: *out = meank; break;
+        case HM_Q_STORAGE_FACTOR: *out = words; break;
+        default: throw HmError{HM_ERR_ARG, "unknown query key"};
+        }
+    });
+}
+
+const char *hm_last_error(hm_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+void hm_destroy(hm_handle h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    try {
+        free_all(h);
+    } catch (...) {
+    }
+    cudaStreamSynchronize(h->stream);
+    if (h->d_counter) cudaFree(h->d_counter);
+    delete h;
+}
+
+hm_status hm_get_nodes_host(hm_handle h, double *out)
+{
+    return guard(h, [&] {
+        if (h->state < 1 || !out) throw HmError{HM_ERR_STATE, "no geometry"};
+        for (int i = 0; i < h->nnode; ++i)
+            for (int c = 0; c < 14; ++c) out[14 * (size_t)i + c] = h->h_nodes[(size_t)c * h->nnode + i];
+    });
+}
+
+hm_status hm_get_near_pairs_host(hm_handle h, int *out)
+{
+    return guard(h, [&] {
+        if (h->state < 1 || !out) throw HmError{HM_ERR_STATE, "no geometry"};
+        for (size_t i = 0; i < h->pair_q.size(); ++i) {
+            out[2 * i] = h->pair_q[i];
+            out[2 * i + 1] = h->pair_p[i];
+        }
+    });
+}
+
+hm_status hm_get_near_block_host(hm_handle h, int tn, int p, void *out)
+{
+    return guard(h, [&] {
+        if (h->state < 2 || !out) throw HmError{HM_ERR_STATE, "near store not filled"};
+        int nc2 = h->nc * h->nc, w = 2 * nc2;
+        if (tn < 0 || tn >= h->nnode || p < 0 || p >= h->npatch) throw HmError{HM_ERR_ARG, "index out of range"};
+        int q = tn / nc2, idx = -1;
+        for (size_t i = 0; i < h->pair_q.size(); ++i)
+            if (h->pair_q[i] == q && h->pair_p[i] == p) idx = (int)i;
+        if (idx < 0) throw HmError{HM_ERR_ARG, "not a near pair"};
+        std::vector<zc> rows(2 * (size_t)w);
+        HM_CUDA(cudaMemcpyAsync(rows.data(), h->d_near + ((size_t)idx * w + 2 * (tn - q * nc2)) * w,
+                                sizeof(zc) * 2 * w, cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        zc *o = (zc *)out;
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a)
+                for (int j = 0; j < nc2; ++j) o[(2 * b + a) * nc2 + j] = rows[(size_t)b * w + 2 * j + a];
+    });
+}
+
+hm_status hm_entries_host(hm_handle h, int n, const int *rows, const int *cols, void *out)
+{
+    return guard(h, [&] {
+        if (h->state < 2) throw HmError{HM_ERR_STATE, "matrix not filled"};
+        if (n <= 0) return;
+        if (!rows || !cols || !out) throw HmError{HM_ERR_ARG, "null pointer"};
+        for (int i = 0; i < n; ++i)
+            if (rows[i] < 0 || rows[i] >= h->N || cols[i] < 0 || cols[i] >= h->N) throw HmError{HM_ERR_ARG, "index out of range"};
+        int *d_rc = (int *)dalloc(h, sizeof(int) * 2 * n);
+        zc *d_o = (zc *)dalloc(h, sizeof(zc) * n);
+        HM_CUDA(cudaMemcpyAsync(d_rc, rows, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+        HM_CUDA(cudaMemcpyAsync(d_rc + n, cols, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+        launch_entries(h, n, d_rc, d_rc + n, d_o);
+        HM_CUDA(cudaMemcpyAsync(out, d_o, sizeof(zc) * n, cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        dfree(h, d_rc);
+        dfree(h, d_o);
+    });
+}
+
+hm_status hm_get_perm_host(hm_handle h, int *perm)
+{
+    return guard(h, [&] {
+        if (h->state < 1 || !perm) throw HmError{HM_ERR_STATE, "no geometry"};
+        HM_CUDA(cudaMemcpyAsync(perm, h->d_perm, sizeof(int) * h->N, cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+hm_status hm_get_blocks_host(hm_handle h, int *nblocks, int *out)
+{
+    return guard(h, [&] {
+        if (h->state < 1 || !nblocks) throw HmError{HM_ERR_STATE, "no geometry"};
+        *nblocks = (int)h->leaves.size();
+        if (!out) return;
+        for (size_t i = 0; i < h->leaves.size(); ++i) {
+            Block *b = h->leaves[i];
+            int *o = out + 6 * i;
+            o[0] = b->type == B_DENSE ? 0 : 1;
+            o[1] = b->r0;
+            o[2] = b->nr;
+            o[3] = b->c0;
+            o[4] = b->nc;
+            o[5] = b->type == B_LR ? b->k : 0;
+        }
+    });
+}
+
+hm_status hm_get_block_dense_host(hm_handle h, int bi, void *out)
+{
+    return guard(h, [&] {
+        if (h->state != 2) throw HmError{HM_ERR_STATE, "blocks are inspectable between hm_fill and hm_factor"};
+        if (bi < 0 || bi >= (int)h->leaves.size() || !out) throw HmError{HM_ERR_ARG, "bad block index"};
+        Block *b = h->leaves[bi];
+        size_t n = (size_t)b->nr * b->nc;
+        zc *d = (zc *)dalloc(h, sizeof(zc) * n);
+        if (b->type == B_DENSE)
+            HM_CUDA(cudaMemcpyAsync(d, b->D, sizeof(zc) * n, cudaMemcpyDeviceToDevice, h->stream));
+        else
+            zgemm(h, 'N', 'C', b->nr, b->nc, b->k, zmake(1, 0), b->U, b->nr, b->V, b->nc, zmake(0, 0), d, b->nr);
+        HM_CUDA(cudaMemcpyAsync(out, d, sizeof(zc) * n, cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        dfree(h, d);
+    });
+}
+
+}  // extern "C"

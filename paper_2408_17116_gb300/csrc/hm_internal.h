@@ -1,0 +1,171 @@
+// Host-side structures of libhm: handle, cluster tree, block tree, error
+// handling, device memory, and the launch wrappers each translation unit exports.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hm.h"
+#include "hm_device.cuh"
+
+struct HmError {
+    hm_status st;
+    std::string msg;
+};
+
+#define HM_CUDA(x)                                                                              \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess)                                                                  \
+            throw HmError{e_ == cudaErrorMemoryAllocation ? HM_ERR_OOM : HM_ERR_CUDA,           \
+                          std::string(#x) + ": " + cudaGetErrorString(e_)};                     \
+    } while (0)
+
+#define HM_CHECK_LAUNCH()                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = cudaGetLastError();                                                    \
+        if (e_ != cudaSuccess)                                                                  \
+            throw HmError{HM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// Quadrature constants of the near-field rule (the GPU method; see hm_near.cu).
+struct NearRule {
+    int qd, qi, qo;     // Duffy points per direction, inner sinh panel points, outer panel points
+    double t0;          // inner panel length (parameter units)
+};
+
+struct Cluster {
+    int off, cnt;       // nodes [off, off+cnt) in tree order
+    double bmin[3], bmax[3];
+    int child[2];
+    int level;
+};
+
+enum BType { B_DENSE = 0, B_LR = 1, B_HIER = 2 };
+
+struct Block {
+    BType type = B_DENSE;
+    int r0 = 0, nr = 0, c0 = 0, nc = 0;  // tree-ordered unknown ranges
+    int t = -1, s = -1;                  // clusters
+    Block *ch[4] = {nullptr, nullptr, nullptr, nullptr};  // (0,0) (0,1) (1,0) (1,1)
+    zc *D = nullptr;                     // dense, column-major, ld = nr
+    int *piv = nullptr;                  // diagonal dense leaf after LU (device, nr entries)
+    zc *U = nullptr, *V = nullptr;       // low rank: A = U V^H, U nr x k, V nc x k
+    int k = 0;
+    int leaf_id = -1;
+    // low-rank updates not yet recompressed: sum_i Up_i Vp_i^H (owned buffers)
+    std::vector<zc *> pu, pv;
+    std::vector<int> pk;
+    int pend_k = 0;
+};
+
+// A dense column-major view in device memory.
+struct MV {
+    zc *p;
+    int rows, cols, ld;
+};
+
+struct hm_handle_s {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int state = 0;  // 0 created, 1 geometry, 2 filled, 3 factored
+    std::string err;
+    hm_params prm{};
+    NearRule rule{24, 24, 16, 0.5};
+    // geometry
+    int nc = 0, nbodies = 0, npatch = 0, nnode = 0, N = 0;
+    std::vector<DevBody> bodies;
+    std::vector<DevPatch> patches;
+    DevBody *d_bodies = nullptr;
+    DevPatch *d_patches = nullptr;
+    double *d_nodes = nullptr;  // SoA [14][nnode]
+    std::vector<double> h_nodes;  // SoA copy
+    // near pairs (CSR by target patch) and store
+    std::vector<int> pair_q, pair_p;  // per pair
+    int *d_pair_q = nullptr, *d_pair_p = nullptr;
+    int *d_nearidx = nullptr;  // [P][P] -> pair index or -1
+    zc *d_near = nullptr;      // [npairs][2 nc^2][2 nc^2]
+    unsigned long long *d_counter = nullptr;  // device counters (quadrature points)
+    // tree
+    std::vector<Cluster> clusters;
+    std::vector<int> perm_node;  // tree position -> natural node
+    int *d_perm = nullptr;       // tree unknown -> natural unknown
+    int *d_iperm = nullptr;      // natural unknown -> tree unknown
+    Block *root = nullptr;
+    std::vector<Block *> blocks;  // all blocks (owned)
+    std::vector<Block *> leaves;
+    Block *copy_root = nullptr;   // unfactored copy (keep_matrix)
+    std::vector<Block *> copy_blocks;
+    // statistics
+    double t_geom = 0, t_near = 0, t_dense = 0, t_aca = 0, t_trunc = 0, t_factor = 0, t_solve = 0;
+    double flops_factor = 0;
+    long long launches = 0;
+    int aca_nonconv = 0;
+    unsigned long long near_points = 0;
+    double tol = 1e-7;
+};
+
+// ---- device memory (stream-ordered pool) ----
+void *dalloc(hm_handle_s *h, size_t bytes);
+void dfree(hm_handle_s *h, void *p);
+
+// ---- hm_geometry.cu ----
+void launch_nodes(hm_handle_s *h, const double *d_x1d, const double *d_w1d);
+void launch_patch_grid(hm_handle_s *h, const double *d_g, int ng, double *d_out);
+void launch_near(hm_handle_s *h, const double *d_tabs, const double *d_C);
+
+// ---- hm_fill.cu ----
+struct DenseDesc {
+    int r0, nr, c0, ncol;
+    zc *D;
+};
+struct LRDesc {
+    int r0, nr, c0, ncol;
+    zc *U, *V;
+    int kmax;
+};
+void launch_dense_fill(hm_handle_s *h, const std::vector<DenseDesc> &descs);
+void launch_aca(hm_handle_s *h, const std::vector<LRDesc> &descs, int *d_rank, int *d_flag);
+void launch_entries(hm_handle_s *h, int n, const int *d_rows, const int *d_cols, zc *d_out);
+
+// ---- hm_linalg.cu (complex FP64 dense kernels) ----
+// C = alpha op(A) op(B) + beta C, op: 'N' or 'C' (conjugate transpose)
+void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, const zc *A, int lda,
+           const zc *B, int ldb, zc beta, zc *C, int ldc);
+void zgetrf(hm_handle_s *h, int n, zc *A, int lda, int *piv, int *d_info);
+void zlaswp(hm_handle_s *h, MV X, const int *piv, int n);  // apply piv[0..n) forward to rows
+void ztrsm_lln(hm_handle_s *h, const zc *L, int ldl, int n, MV X);   // X = L^-1 X, unit lower
+void ztrsm_lun(hm_handle_s *h, const zc *U, int ldu, int n, MV X);   // X = U^-1 X, upper
+void ztrsm_luh(hm_handle_s *h, const zc *U, int ldu, int n, MV X);   // X = U^-H X
+void ztrsm_run(hm_handle_s *h, const zc *U, int ldu, int n, MV X);   // X = X U^-1 (X rows x n)
+void zcopy2d(hm_handle_s *h, MV dst, MV src);
+void zscale_cols(hm_handle_s *h, MV X, const double *d_s);           // X[:,j] *= s[j]
+// Truncated recompression of A = U V^H (U m x K, V n x K): returns the new rank;
+// *Uo, *Vo receive freshly allocated factors (balanced: both scaled by sqrt(sigma)).
+int truncate_lr(hm_handle_s *h, int m, int n, int K, const zc *U, int ldu, const zc *V, int ldv,
+                double tol, int kmax, zc **Uo, zc **Vo);
+void batched_truncate(hm_handle_s *h, std::vector<Block *> &blks, const std::vector<int> &ranks, double tol);
+
+// ---- hm_io.cu ----
+void launch_rhs(hm_handle_s *h, int nrhs, const double *d_dirs, zc *d_b);  // tree order
+void launch_permute(hm_handle_s *h, int nrhs, const zc *src, zc *dst, const int *map);
+void launch_farfield(hm_handle_s *h, int nrhs, const zc *d_x, int nang, const double *d_dirs, zc *d_efar,
+                     double *d_rcs);
+
+// ---- hm_hlu.cpp ----
+void hlu_factor(hm_handle_s *h);
+void hsolve(hm_handle_s *h, MV X);                 // X (tree order) <- A^-1 X
+void hmatvec(hm_handle_s *h, Block *A, MV X, MV Y, zc alpha, bool conjtrans);  // Y += alpha op(A) X
+Block *clone_tree(hm_handle_s *h, Block *b, std::vector<Block *> &owned);
+void free_tree(hm_handle_s *h, std::vector<Block *> &owned);
+
+// ---- hm_planner.cpp ----
+void plan_geometry(hm_handle_s *h);  // nodes, near pairs, cluster tree, block tree
+void rebuild_block_tree(hm_handle_s *h);  // block tree from the cluster tree (discards blocks)
+void cheb_nodes_host(int n, double *x);
+void fejer_weights_host(int n, double *w);
+void gauss_legendre_host(int q, double *x, double *w);
+
+static inline void count_launch(hm_handle_s *h, int n = 1) { h->launches += n; }

@@ -1,0 +1,834 @@
+// Complex FP64 dense kernels for the H-matrix arithmetic: GEMM, leaf LU with
+// partial pivoting, triangular solves, Householder QR, one-sided Jacobi SVD and
+// the truncated recompression of low-rank sums (Sec. III: "fast formatted matrix
+// addition and multiplication", H-LU of ref. [23]).
+//
+// On GB300 FP64 runs on the CUDA-core FP64 pipe; these kernels are bound by it.
+#include <algorithm>
+#include <cmath>
+
+#include "hm_internal.h"
+
+// ---------------------------------------------------------------------------
+// GEMM: C = alpha op(A) op(B) + beta C, 64 x 64 tiles, BK = 8, 256 threads,
+// 4 x 4 outputs per thread; optional deterministic split-K through a workspace.
+// ---------------------------------------------------------------------------
+#define GB_M 64
+#define GB_N 64
+#define GB_K 8
+
+struct GemmArgs {
+    int opA, opB;  // 0 'N', 1 'C'
+    int m, n, k;
+    zc alpha, beta;
+    const zc *A;
+    int lda;
+    const zc *B;
+    int ldb;
+    zc *C;
+    int ldc;
+    zc *work;      // split-K partials [splits][m][n] (column-major m x n each), or null
+    int kchunk;
+};
+
+__device__ __forceinline__ zc loadA(const GemmArgs &g, int i, int p)
+{
+    if (i >= g.m || p >= g.k) return zmake(0, 0);
+    return g.opA ? zconj(g.A[(size_t)i * g.lda + p]) : g.A[(size_t)p * g.lda + i];
+}
+__device__ __forceinline__ zc loadB(const GemmArgs &g, int p, int j)
+{
+    if (j >= g.n || p >= g.k) return zmake(0, 0);
+    return g.opB ? zconj(g.B[(size_t)p * g.ldb + j]) : g.B[(size_t)j * g.ldb + p];
+}
+
+__global__ void __launch_bounds__(256) k_zgemm(GemmArgs g)
+{
+    __shared__ zc As[GB_K][GB_M];
+    __shared__ zc Bs[GB_K][GB_N + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.x * GB_M, j0 = blockIdx.y * GB_N;
+    const int kb = blockIdx.z * g.kchunk, ke = min(g.k, kb + g.kchunk);
+    zc acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = zmake(0, 0);
+    for (int p0 = kb; p0 < ke; p0 += GB_K) {
+        // load 64 x 8 of A and 8 x 64 of B: 512 elements each, 2 per thread
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int e = tid + r * 256;
+            int ii = e & 63, pp = e >> 6;
+            int gp = p0 + pp;
+            As[pp][ii] = (gp < ke) ? loadA(g, i0 + ii, gp) : zmake(0, 0);
+            int jj = e & 63;
+            Bs[pp][jj] = (gp < ke) ? loadB(g, gp, j0 + jj) : zmake(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int pp = 0; pp < GB_K; ++pp) {
+            zc a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = As[pp][tx + 16 * q];
+                b[q] = Bs[pp][ty + 16 * q];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = zfma(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        int i = i0 + tx + 16 * x;
+        if (i >= g.m) continue;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            int j = j0 + ty + 16 * y;
+            if (j >= g.n) continue;
+            if (g.work) {
+                g.work[(size_t)blockIdx.z * g.m * g.n + (size_t)j * g.m + i] = acc[x][y];
+            } else {
+                zc v = zmul(g.alpha, acc[x][y]);
+                zc *c = g.C + (size_t)j * g.ldc + i;
+                if (g.beta.x != 0.0 || g.beta.y != 0.0) v = zfma(g.beta, *c, v);
+                *c = v;
+            }
+        }
+    }
+}
+
+__global__ void k_splitk_reduce(GemmArgs g, int splits)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t mn = (size_t)g.m * g.n;
+    if (idx >= mn) return;
+    zc s = zmake(0, 0);
+    for (int z = 0; z < splits; ++z) s = zadd(s, g.work[(size_t)z * mn + idx]);
+    int i = (int)(idx % g.m), j = (int)(idx / g.m);
+    zc v = zmul(g.alpha, s);
+    zc *c = g.C + (size_t)j * g.ldc + i;
+    if (g.beta.x != 0.0 || g.beta.y != 0.0) v = zfma(g.beta, *c, v);
+    *c = v;
+}
+
+__global__ void k_scale(zc *C, int m, int n, int ldc, zc beta)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)m * n) return;
+    int i = (int)(idx % m), j = (int)(idx / m);
+    zc *c = C + (size_t)j * ldc + i;
+    *c = (beta.x == 0.0 && beta.y == 0.0) ? zmake(0, 0) : zmul(beta, *c);
+}
+
+void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, const zc *A, int lda, const zc *B,
+           int ldb, zc beta, zc *C, int ldc)
+{
+    if (m <= 0 || n <= 0) return;
+    if (k <= 0) {
+        size_t mn = (size_t)m * n;
+        k_scale<<<(unsigned)((mn + 255) / 256), 256, 0, h->stream>>>(C, m, n, ldc, beta);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+        return;
+    }
+    GemmArgs g;
+    g.opA = (opA == 'C');
+    g.opB = (opB == 'C');
+    g.m = m;
+    g.n = n;
+    g.k = k;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.A = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.C = C;
+    g.ldc = ldc;
+    int gm = (m + GB_M - 1) / GB_M, gn = (n + GB_N - 1) / GB_N;
+    int tiles = gm * gn;
+    int splits = 1;
+    // split K when the output has few tiles and the inner dimension is long
+    if (tiles < 76 && k >= 512) splits = std::min(std::max(1, 152 / tiles), std::max(1, k / 256));
+    h->flops_factor += 8.0 * m * n * k;
+    if (splits > 1) {
+        g.kchunk = ((k + splits - 1) / splits + GB_K - 1) / GB_K * GB_K;
+        splits = (k + g.kchunk - 1) / g.kchunk;
+        g.work = (zc *)dalloc(h, sizeof(zc) * (size_t)m * n * splits);
+        k_zgemm<<<dim3(gm, gn, splits), 256, 0, h->stream>>>(g);
+        HM_CHECK_LAUNCH();
+        size_t mn = (size_t)m * n;
+        k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, h->stream>>>(g, splits);
+        HM_CHECK_LAUNCH();
+        count_launch(h, 2);
+        dfree(h, g.work);
+    } else {
+        g.work = nullptr;
+        g.kchunk = k;
+        k_zgemm<<<dim3(gm, gn, 1), 256, 0, h->stream>>>(g);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LU with partial pivoting of one n x n leaf (n <= 1024), one CTA.
+// Pivot: largest modulus in the column, ties to the lowest row.  piv[k] = row
+// swapped with k (0-based, applied in order k = 0..n-1).  info: 0 or k+1 on a zero pivot.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_getrf(int n, zc *A, int lda, int *piv, int *info)
+{
+    __shared__ double sv[33];
+    __shared__ int si[33];
+    __shared__ int s_p;
+    __shared__ zc s_inv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+        // argmax |A[i,k]|, i >= k
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int i = k + tid; i < n; i += nt) {
+            double v = zabs2(A[(size_t)k * lda + i]);
+            if (v > bv || (v == bv && i < bi)) {
+                bv = v;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double v2 = __shfl_down_sync(0xffffffff, bv, o);
+            int i2 = __shfl_down_sync(0xffffffff, bi, o);
+            if (v2 > bv || (v2 == bv && i2 < bi)) {
+                bv = v2;
+                bi = i2;
+            }
+        }
+        if ((tid & 31) == 0) {
+            sv[tid >> 5] = bv;
+            si[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double v = sv[0];
+            int ii = si[0];
+            for (int w = 1; w < (nt + 31) / 32; ++w)
+                if (sv[w] > v || (sv[w] == v && si[w] < ii)) {
+                    v = sv[w];
+                    ii = si[w];
+                }
+            s_p = ii;
+            piv[k] = ii;
+            if (!(v > 0.0)) {
+                if (!bad) *info = k + 1;
+                bad = 1;
+                s_inv = zmake(0, 0);
+            } else {
+                zc pv = A[(size_t)k * lda + ii];
+                s_inv = zdiv(zmake(1, 0), pv);
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < n; j += nt) {
+                zc t = A[(size_t)j * lda + k];
+                A[(size_t)j * lda + k] = A[(size_t)j * lda + p];
+                A[(size_t)j * lda + p] = t;
+            }
+        __syncthreads();
+        const zc inv = s_inv;
+        for (int i = k + 1 + tid; i < n; i += nt) A[(size_t)k * lda + i] = zmul(A[(size_t)k * lda + i], inv);
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            int i = k + 1 + e % m, j = k + 1 + e / m;
+            A[(size_t)j * lda + i] = zsub(A[(size_t)j * lda + i], zmul(A[(size_t)k * lda + i], A[(size_t)j * lda + k]));
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && !bad && info) {
+        // keep info untouched when zero (caller initialised)
+    }
+}
+
+void zgetrf(hm_handle_s *h, int n, zc *A, int lda, int *piv, int *d_info)
+{
+    if (n <= 0) return;
+    int T = n >= 512 ? 1024 : (n >= 128 ? 512 : 256);
+    k_getrf<<<1, T, 0, h->stream>>>(n, A, lda, piv, d_info);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    h->flops_factor += 8.0 / 3.0 * n * (double)n * n;
+}
+
+// ---------------------------------------------------------------------------
+// Row interchanges and triangular solves on multi-vectors X (rows x cols, ld)
+// ---------------------------------------------------------------------------
+__global__ void k_laswp(zc *X, int ld, int cols, const int *piv, int n)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    zc *x = X + (size_t)j * ld;
+    for (int k = 0; k < n; ++k) {
+        int p = piv[k];
+        if (p != k) {
+            zc t = x[k];
+            x[k] = x[p];
+            x[p] = t;
+        }
+    }
+}
+
+void zlaswp(hm_handle_s *h, MV X, const int *piv, int n)
+{
+    if (X.cols <= 0 || n <= 0) return;
+    k_laswp<<<(X.cols + 127) / 128, 128, 0, h->stream>>>(X.p, X.ld, X.cols, piv, n);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+}
+
+// Left solves: one CTA per group of TRS_CB columns; the columns live in shared memory.
+#define TRS_CB 8
+#define TRS_T 256
+
+// mode 0: X = L^-1 X (unit lower); 1: X = U^-1 X (upper); 2: X = U^-H X (U^H lower, non-unit)
+__global__ void __launch_bounds__(TRS_T) k_trsm_left(int mode, const zc *__restrict__ T, int ldt, int n, zc *X, int ldx,
+                                                      int cols)
+{
+    extern __shared__ zc xs[];  // [TRS_CB][n]
+    const int c0 = blockIdx.x * TRS_CB;
+    const int nc = min(TRS_CB, cols - c0);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nc * n; e += TRS_T) {
+        int c = e / n, i = e - c * n;
+        xs[c * n + i] = X[(size_t)(c0 + c) * ldx + i];
+    }
+    __syncthreads();
+    if (mode == 0) {
+        for (int j = 0; j < n; ++j) {
+            for (int e = tid; e < nc * (n - j - 1); e += TRS_T) {
+                int c = e / (n - j - 1), i = j + 1 + e % (n - j - 1);
+                xs[c * n + i] = zsub(xs[c * n + i], zmul(T[(size_t)j * ldt + i], xs[c * n + j]));
+            }
+            __syncthreads();
+        }
+    } else if (mode == 1) {
+        for (int j = n - 1; j >= 0; --j) {
+            if (tid < nc) xs[tid * n + j] = zdiv(xs[tid * n + j], T[(size_t)j * ldt + j]);
+            __syncthreads();
+            for (int e = tid; e < nc * j; e += TRS_T) {
+                int c = e / j, i = e % j;
+                xs[c * n + i] = zsub(xs[c * n + i], zmul(T[(size_t)j * ldt + i], xs[c * n + j]));
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int j = 0; j < n; ++j) {
+            if (tid < nc) xs[tid * n + j] = zdiv(xs[tid * n + j], zconj(T[(size_t)j * ldt + j]));
+            __syncthreads();
+            for (int e = tid; e < nc * (n - j - 1); e += TRS_T) {
+                int c = e / (n - j - 1), i = j + 1 + e % (n - j - 1);
+                // (U^H)[i,j] = conj(U[j,i])
+                xs[c * n + i] = zsub(xs[c * n + i], zmul(zconj(T[(size_t)i * ldt + j]), xs[c * n + j]));
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < nc * n; e += TRS_T) {
+        int c = e / n, i = e - c * n;
+        X[(size_t)(c0 + c) * ldx + i] = xs[c * n + i];
+    }
+}
+
+static void trsm_left(hm_handle_s *h, int mode, const zc *T, int ldt, int n, MV X)
+{
+    if (X.cols <= 0 || n <= 0) return;
+    size_t smem = sizeof(zc) * TRS_CB * n;
+    if (smem > 48 * 1024) HM_CUDA(cudaFuncSetAttribute(k_trsm_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_trsm_left<<<(X.cols + TRS_CB - 1) / TRS_CB, TRS_T, smem, h->stream>>>(mode, T, ldt, n, X.p, X.ld, X.cols);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    h->flops_factor += 4.0 * n * (double)n * X.cols;
+}
+
+void ztrsm_lln(hm_handle_s *h, const zc *L, int ldl, int n, MV X) { trsm_left(h, 0, L, ldl, n, X); }
+void ztrsm_lun(hm_handle_s *h, const zc *U, int ldu, int n, MV X) { trsm_left(h, 1, U, ldu, n, X); }
+void ztrsm_luh(hm_handle_s *h, const zc *U, int ldu, int n, MV X) { trsm_left(h, 2, U, ldu, n, X); }
+
+// X = X U^-1 (X rows x n): one thread per row, sequential over columns.
+__global__ void k_trsm_right_upper(const zc *__restrict__ U, int ldu, int n, zc *X, int ldx, int rows)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    for (int j = 0; j < n; ++j) {
+        zc s = X[(size_t)j * ldx + r];
+        for (int i = 0; i < j; ++i) s = zsub(s, zmul(X[(size_t)i * ldx + r], U[(size_t)j * ldu + i]));
+        X[(size_t)j * ldx + r] = zdiv(s, U[(size_t)j * ldu + j]);
+    }
+}
+
+void ztrsm_run(hm_handle_s *h, const zc *U, int ldu, int n, MV X)
+{
+    if (X.rows <= 0 || n <= 0) return;
+    k_trsm_right_upper<<<(X.rows + 63) / 64, 64, 0, h->stream>>>(U, ldu, n, X.p, X.ld, X.rows);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    h->flops_factor += 4.0 * n * (double)n * X.rows;
+}
+
+__global__ void k_copy2d(zc *dst, int ldd, const zc *src, int lds, int rows, int cols)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * cols) return;
+    int i = (int)(idx % rows), j = (int)(idx / rows);
+    dst[(size_t)j * ldd + i] = src[(size_t)j * lds + i];
+}
+
+void zcopy2d(hm_handle_s *h, MV dst, MV src)
+{
+    size_t n = (size_t)src.rows * src.cols;
+    if (n == 0) return;
+    k_copy2d<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dst.p, dst.ld, src.p, src.ld, src.rows, src.cols);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+}
+
+__global__ void k_scale_cols(zc *X, int ld, int rows, int cols, const double *s)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * cols) return;
+    int i = (int)(idx % rows), j = (int)(idx / rows);
+    X[(size_t)j * ld + i] = zscale(X[(size_t)j * ld + i], s[j]);
+}
+
+void zscale_cols(hm_handle_s *h, MV X, const double *d_s)
+{
+    size_t n = (size_t)X.rows * X.cols;
+    if (n == 0) return;
+    k_scale_cols<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(X.p, X.ld, X.rows, X.cols, d_s);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR, one CTA per matrix: A (m x K, ld m) -> Q (m x r), R (r x K), r = min(m, K).
+// H_j = I - 2 v v^H / (v^H v), v = x - alpha e_1, alpha = -exp(i arg x_0) |x|, H_j x = alpha e_1.
+// ---------------------------------------------------------------------------
+struct QRDesc {
+    zc *A;       // input, overwritten (reflectors)
+    int m, K;
+    zc *Q;       // m x r
+    zc *R;       // r x K
+    double *beta;  // workspace [r]
+};
+
+#define QR_T 512
+
+__device__ double qr_block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffff, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < QR_T / 32; ++w) s += sh[w];
+        sh[32] = s;
+    }
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(QR_T) k_qr(const QRDesc *__restrict__ descs)
+{
+    const QRDesc d = descs[blockIdx.x];
+    const int m = d.m, K = d.K, r = min(m, K);
+    __shared__ double sh[33];
+    __shared__ zc s_alpha;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_T / 32;
+    zc *A = d.A;
+    for (int j = 0; j < r; ++j) {
+        zc *x = A + (size_t)j * m;
+        double nrm2 = 0.0;
+        for (int i = j + tid; i < m; i += QR_T) nrm2 += zabs2(x[i]);
+        nrm2 = qr_block_sum(nrm2, sh);
+        double nrm = sqrt(nrm2);
+        if (tid == 0) {
+            zc x0 = x[j];
+            double a0 = sqrt(zabs2(x0));
+            zc ph = a0 > 0 ? zscale(x0, 1.0 / a0) : zmake(1, 0);
+            zc alpha = zscale(ph, -nrm);
+            s_alpha = alpha;
+            // v = x - alpha e1; v^H v = 2 (|x|^2 + |x| |x0|)
+            x[j] = zsub(x0, alpha);
+            double vhv = 2.0 * (nrm2 + nrm * a0);
+            d.beta[j] = vhv > 0 ? 2.0 / vhv : 0.0;
+        }
+        __syncthreads();
+        const double beta = d.beta[j];
+        // apply H to columns c > j: a -= beta v (v^H a)
+        for (int c = j + 1 + warp; c < K; c += nw) {
+            zc *a = A + (size_t)c * m;
+            zc s = zmake(0, 0);
+            for (int i = j + lane; i < m; i += 32) s = zfmac(x[i], a[i], s);
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffff, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffff, s.y, o);
+            }
+            s = zscale(s, beta);
+            for (int i = j + lane; i < m; i += 32) a[i] = zsub(a[i], zmul(x[i], s));
+        }
+        __syncthreads();
+        // R row j
+        if (tid == 0) d.R[(size_t)j * r + j] = s_alpha;
+        for (int c = j + 1 + tid; c < K; c += QR_T) d.R[(size_t)c * r + j] = A[(size_t)c * m + j];
+        for (int c = tid; c < j && c < K; c += QR_T) d.R[(size_t)c * r + j] = zmake(0, 0);
+        __syncthreads();
+    }
+    // Q = H_0 ... H_{r-1} [I_r; 0]
+    for (int e = tid; e < m * r; e += QR_T) {
+        int i = e % m, c = e / m;
+        d.Q[(size_t)c * m + i] = zmake(i == c ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    for (int j = r - 1; j >= 0; --j) {
+        const zc *v = A + (size_t)j * m;
+        const double beta = d.beta[j];
+        for (int c = j + warp; c < r; c += nw) {
+            zc *q = d.Q + (size_t)c * m;
+            zc s = zmake(0, 0);
+            for (int i = j + lane; i < m; i += 32) s = zfmac(v[i], q[i], s);
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffff, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffff, s.y, o);
+            }
+            s = zscale(s, beta);
+            for (int i = j + lane; i < m; i += 32) q[i] = zsub(q[i], zmul(v[i], s));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi SVD, one CTA per matrix: M (p x q, ld p) -> M Y = X Sigma with
+// Y (q x q) unitary; on exit M holds X Sigma (orthogonal columns), S[j] = |col j|,
+// ord[] = column order by decreasing S.  Round-robin pairs, one warp per pair.
+// ---------------------------------------------------------------------------
+struct SVDDesc {
+    zc *M;
+    int p, q;
+    zc *Y;
+    double *S;
+    int *ord;
+};
+
+#define SVD_T 512
+#define SVD_QMAX 4096
+
+__global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc *__restrict__ descs)
+{
+    const SVDDesc d = descs[blockIdx.x];
+    const int p = d.p, q = d.q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = SVD_T / 32;
+    __shared__ int s_rot;
+    extern __shared__ int perm[];  // [q rounded up to even]
+    for (int e = tid; e < q * q; e += SVD_T) {
+        int i = e % q, j = e / q;
+        d.Y[(size_t)j * q + i] = zmake(i == j ? 1.0 : 0.0, 0.0);
+    }
+    const int qe = (q + 1) & ~1;  // even count (a dummy column when q is odd)
+    for (int i = tid; i < qe; i += SVD_T) perm[i] = i;
+    __syncthreads();
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < qe - 1; ++round) {
+            for (int pr = warp; pr < qe / 2; pr += nw) {
+                int a = perm[pr], b = perm[qe - 1 - pr];
+                if (a >= q || b >= q) continue;
+                if (a > b) {
+                    int t = a;
+                    a = b;
+                    b = t;
+                }
+                zc *ca = d.M + (size_t)a * p, *cb = d.M + (size_t)b * p;
+                double al = 0, be = 0;
+                zc ga = zmake(0, 0);
+                for (int i = lane; i < p; i += 32) {
+                    al += zabs2(ca[i]);
+                    be += zabs2(cb[i]);
+                    ga = zfmac(ca[i], cb[i], ga);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffff, al, o);
+                    be += __shfl_xor_sync(0xffffffff, be, o);
+                    ga.x += __shfl_xor_sync(0xffffffff, ga.x, o);
+                    ga.y += __shfl_xor_sync(0xffffffff, ga.y, o);
+                }
+                double g = sqrt(zabs2(ga));
+                if (!(g > 1e-15 * sqrt(al * be)) || g == 0.0) continue;
+                if (lane == 0) s_rot = 1;
+                zc eph = zscale(ga, 1.0 / g);  // exp(i phi)
+                double zeta = (be - al) / (2.0 * g);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                zc sem = zscale(zconj(eph), s), sep = zscale(eph, s);
+                for (int i = lane; i < p; i += 32) {
+                    zc x = ca[i], y = cb[i];
+                    ca[i] = zsub(zscale(x, c), zmul(sem, y));
+                    cb[i] = zadd(zmul(sep, x), zscale(y, c));
+                }
+                zc *ya = d.Y + (size_t)a * q, *yb = d.Y + (size_t)b * q;
+                for (int i = lane; i < q; i += 32) {
+                    zc x = ya[i], y = yb[i];
+                    ya[i] = zsub(zscale(x, c), zmul(sem, y));
+                    yb[i] = zadd(zmul(sep, x), zscale(y, c));
+                }
+            }
+            __syncthreads();
+            // rotate the round-robin order (position 0 fixed)
+            if (tid == 0) {
+                int last = perm[qe - 1];
+                for (int i = qe - 1; i > 1; --i) perm[i] = perm[i - 1];
+                perm[1] = last;
+            }
+            __syncthreads();
+        }
+        if (!s_rot) break;
+        __syncthreads();
+    }
+    for (int j = warp; j < q; j += nw) {
+        double s = 0;
+        for (int i = lane; i < p; i += 32) s += zabs2(d.M[(size_t)j * p + i]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
+        if (lane == 0) d.S[j] = sqrt(s);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // insertion sort of indices by decreasing S (q is small)
+        for (int j = 0; j < q; ++j) d.ord[j] = j;
+        for (int j = 1; j < q; ++j) {
+            int v = d.ord[j];
+            int i = j - 1;
+            while (i >= 0 && d.S[d.ord[i]] < d.S[v]) {
+                d.ord[i + 1] = d.ord[i];
+                --i;
+            }
+            d.ord[i + 1] = v;
+        }
+    }
+}
+
+// Assemble the truncated factors: Uo[:, t] = Q_U * (X col ord[t]) / S * sqrt(S) ... done as
+// gather + scale: G[:, t] = M[:, ord[t]] * f(S), H[:, t] = Y[:, ord[t]] * sqrt(S)
+__global__ void k_gather_cols(const zc *M, int p, const int *ord, const double *S, int kk, zc *G, int mode)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)p * kk) return;
+    int i = (int)(idx % p), t = (int)(idx / p);
+    int c = ord[t];
+    double s = S[c];
+    double f;
+    if (mode == 0)
+        f = s > 0 ? 1.0 / sqrt(s) : 0.0;  // X Sigma -> X sqrt(Sigma)
+    else
+        f = sqrt(s);  // Y -> Y sqrt(Sigma)
+    G[(size_t)t * p + i] = zscale(M[(size_t)c * p + i], f);
+}
+
+// ---------------------------------------------------------------------------
+// Truncated recompression of U V^H (batched): QR of both factors, SVD of the core
+// R_U R_V^H, keep the smallest rank k' with sqrt(sum_{i>k'} s_i^2) <= tol |s|_2.
+// ---------------------------------------------------------------------------
+struct TruncJob {
+    int m, n, K;
+    const zc *U;
+    int ldu;
+    const zc *V;
+    int ldv;
+    int kmax;
+    // work
+    zc *Ua, *Va, *QU, *QV, *RU, *RV, *Mc, *Y;
+    double *bU, *bV, *S;
+    int *ord;
+    int r1, r2;
+};
+
+static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob> &jobs)
+{
+    // workspace and copies
+    std::vector<QRDesc> qd;
+    for (auto &J : jobs) {
+        J.r1 = std::min(J.m, J.K);
+        J.r2 = std::min(J.n, J.K);
+        J.Ua = (zc *)dalloc(h, sizeof(zc) * (size_t)J.m * J.K);
+        J.Va = (zc *)dalloc(h, sizeof(zc) * (size_t)J.n * J.K);
+        J.QU = (zc *)dalloc(h, sizeof(zc) * (size_t)J.m * J.r1);
+        J.QV = (zc *)dalloc(h, sizeof(zc) * (size_t)J.n * J.r2);
+        J.RU = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r1 * J.K);
+        J.RV = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r2 * J.K);
+        J.Mc = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r1 * J.r2);
+        J.Y = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r2 * J.r2);
+        J.bU = (double *)dalloc(h, sizeof(double) * (J.r1 + J.r2 + J.r2));
+        J.bV = J.bU + J.r1;
+        J.S = J.bV + J.r2;
+        J.ord = (int *)dalloc(h, sizeof(int) * J.r2);
+        zcopy2d(h, MV{J.Ua, J.m, J.K, J.m}, MV{(zc *)J.U, J.m, J.K, J.ldu});
+        zcopy2d(h, MV{J.Va, J.n, J.K, J.n}, MV{(zc *)J.V, J.n, J.K, J.ldv});
+        qd.push_back(QRDesc{J.Ua, J.m, J.K, J.QU, J.RU, J.bU});
+        qd.push_back(QRDesc{J.Va, J.n, J.K, J.QV, J.RV, J.bV});
+        h->flops_factor += 16.0 * ((double)J.m + J.n) * J.K * J.K;
+    }
+    QRDesc *d_qd = (QRDesc *)dalloc(h, sizeof(QRDesc) * qd.size());
+    HM_CUDA(cudaMemcpyAsync(d_qd, qd.data(), sizeof(QRDesc) * qd.size(), cudaMemcpyHostToDevice, h->stream));
+    k_qr<<<(unsigned)qd.size(), QR_T, 0, h->stream>>>(d_qd);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    // core M = R_U R_V^H
+    for (auto &J : jobs)
+        zgemm(h, 'N', 'C', J.r1, J.r2, J.K, zmake(1, 0), J.RU, J.r1, J.RV, J.r2, zmake(0, 0), J.Mc, J.r1);
+    std::vector<SVDDesc> sd;
+    for (auto &J : jobs) sd.push_back(SVDDesc{J.Mc, J.r1, J.r2, J.Y, J.S, J.ord});
+    int qmax = 0;
+    for (auto &J : jobs) qmax = std::max(qmax, J.r2);
+    if (qmax > SVD_QMAX) throw HmError{HM_ERR_NUMERIC, "recompression core too large: " + std::to_string(qmax)};
+    SVDDesc *d_sd = (SVDDesc *)dalloc(h, sizeof(SVDDesc) * sd.size());
+    HM_CUDA(cudaMemcpyAsync(d_sd, sd.data(), sizeof(SVDDesc) * sd.size(), cudaMemcpyHostToDevice, h->stream));
+    k_svd<<<(unsigned)sd.size(), SVD_T, sizeof(int) * (qmax + 2), h->stream>>>(d_sd);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    dfree(h, d_qd);
+    dfree(h, d_sd);
+}
+
+// returns the kept rank; allocates *Uo (m x k'), *Vo (n x k')
+static int trunc_stage2(hm_handle_s *h, TruncJob &J, const std::vector<double> &S, const std::vector<int> &ord,
+                        double tol, zc **Uo, zc **Vo)
+{
+    double tot = 0;
+    for (double s : S) tot += s * s;
+    int kk = (int)S.size();
+    double tail = 0;
+    while (kk > 0) {
+        double s = S[ord[kk - 1]];
+        if (tail + s * s > tol * tol * tot) break;
+        tail += s * s;
+        --kk;
+    }
+    if (tot == 0.0) kk = 0;
+    kk = std::min(kk, J.kmax > 0 ? J.kmax : kk);
+    zc *G = nullptr, *Hh = nullptr;
+    *Uo = nullptr;
+    *Vo = nullptr;
+    if (kk > 0) {
+        G = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r1 * kk);
+        Hh = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r2 * kk);
+        size_t n1 = (size_t)J.r1 * kk, n2 = (size_t)J.r2 * kk;
+        k_gather_cols<<<(unsigned)((n1 + 255) / 256), 256, 0, h->stream>>>(J.Mc, J.r1, J.ord, J.S, kk, G, 0);
+        k_gather_cols<<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(J.Y, J.r2, J.ord, J.S, kk, Hh, 1);
+        HM_CHECK_LAUNCH();
+        count_launch(h, 2);
+        *Uo = (zc *)dalloc(h, sizeof(zc) * (size_t)J.m * kk);
+        *Vo = (zc *)dalloc(h, sizeof(zc) * (size_t)J.n * kk);
+        zgemm(h, 'N', 'N', J.m, kk, J.r1, zmake(1, 0), J.QU, J.m, G, J.r1, zmake(0, 0), *Uo, J.m);
+        zgemm(h, 'N', 'N', J.n, kk, J.r2, zmake(1, 0), J.QV, J.n, Hh, J.r2, zmake(0, 0), *Vo, J.n);
+        dfree(h, G);
+        dfree(h, Hh);
+    }
+    dfree(h, J.Ua);
+    dfree(h, J.Va);
+    dfree(h, J.QU);
+    dfree(h, J.QV);
+    dfree(h, J.RU);
+    dfree(h, J.RV);
+    dfree(h, J.Mc);
+    dfree(h, J.Y);
+    dfree(h, J.bU);
+    dfree(h, J.ord);
+    return kk;
+}
+
+static void fetch_sv(hm_handle_s *h, std::vector<TruncJob> &jobs, std::vector<std::vector<double>> &S,
+                     std::vector<std::vector<int>> &ord)
+{
+    S.resize(jobs.size());
+    ord.resize(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        S[i].resize(jobs[i].r2);
+        ord[i].resize(jobs[i].r2);
+        HM_CUDA(cudaMemcpyAsync(S[i].data(), jobs[i].S, sizeof(double) * jobs[i].r2, cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaMemcpyAsync(ord[i].data(), jobs[i].ord, sizeof(int) * jobs[i].r2, cudaMemcpyDeviceToHost, h->stream));
+    }
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+int truncate_lr(hm_handle_s *h, int m, int n, int K, const zc *U, int ldu, const zc *V, int ldv, double tol, int kmax,
+                zc **Uo, zc **Vo)
+{
+    *Uo = *Vo = nullptr;
+    if (K <= 0 || m <= 0 || n <= 0) return 0;
+    std::vector<TruncJob> jobs(1);
+    jobs[0] = TruncJob{};
+    jobs[0].m = m;
+    jobs[0].n = n;
+    jobs[0].K = K;
+    jobs[0].U = U;
+    jobs[0].ldu = ldu;
+    jobs[0].V = V;
+    jobs[0].ldv = ldv;
+    jobs[0].kmax = kmax;
+    trunc_stage1(h, jobs);
+    std::vector<std::vector<double>> S;
+    std::vector<std::vector<int>> ord;
+    fetch_sv(h, jobs, S, ord);
+    return trunc_stage2(h, jobs[0], S[0], ord[0], tol, Uo, Vo);
+}
+
+// Recompress the low-rank leaves blks (U, V with ranks[i] columns) in one batch;
+// replaces b->U, b->V, b->k.
+void batched_truncate(hm_handle_s *h, std::vector<Block *> &blks, const std::vector<int> &ranks, double tol)
+{
+    const size_t CH = 512;  // jobs per batch (bounds the workspace)
+    for (size_t s = 0; s < blks.size(); s += CH) {
+        size_t e = std::min(blks.size(), s + CH);
+        std::vector<TruncJob> jobs;
+        std::vector<size_t> idx;
+        for (size_t i = s; i < e; ++i) {
+            Block *b = blks[i];
+            if (ranks[i] <= 0) continue;
+            TruncJob J{};
+            J.m = b->nr;
+            J.n = b->nc;
+            J.K = ranks[i];
+            J.U = b->U;
+            J.ldu = b->nr;
+            J.V = b->V;
+            J.ldv = b->nc;
+            J.kmax = 0;
+            jobs.push_back(J);
+            idx.push_back(i);
+        }
+        if (jobs.empty()) continue;
+        trunc_stage1(h, jobs);
+        std::vector<std::vector<double>> S;
+        std::vector<std::vector<int>> ord;
+        fetch_sv(h, jobs, S, ord);
+        for (size_t t = 0; t < jobs.size(); ++t) {
+            Block *b = blks[idx[t]];
+            zc *Uo, *Vo;
+            int kk = trunc_stage2(h, jobs[t], S[t], ord[t], tol, &Uo, &Vo);
+            dfree(h, b->U);
+            dfree(h, b->V);
+            b->U = Uo;
+            b->V = Vo;
+            b->k = kk;
+        }
+    }
+}

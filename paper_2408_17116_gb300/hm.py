@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libhm (include/hm.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library; PyTorch supplies device
+buffers (complex128 tensors) and the stream.  Importing this module raises if
+libhm.so has not been built: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "libhm.so")
+
+HM_OK = 0
+STATUS = {0: "HM_OK", 1: "HM_ERR_ARG", 2: "HM_ERR_STATE", 3: "HM_ERR_CUDA", 4: "HM_ERR_OOM",
+          5: "HM_ERR_SINGULAR", 6: "HM_ERR_NOT_CONVERGED", 7: "HM_ERR_TIMEOUT", 8: "HM_ERR_NUMERIC"}
+Q = dict(N=0, NNODE=1, NPATCH=2, NEAR_PAIRS=3, DENSE_BLOCKS=4, LR_BLOCKS=5, CR=6, MAX_RANK=7,
+         T_GEOMETRY=8, T_NEAR=9, T_DENSE=10, T_ACA=11, T_FACTOR=12, T_SOLVE=13, FLOPS_FACTOR=14,
+         STORAGE=15, ACA_NONCONV=16, LAUNCHES=17, NEAR_QPOINTS=18, MEAN_RANK=19, STORAGE_FACTOR=20,
+         T_RECOMPRESS=21)
+
+EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor", "hm_solve",
+           "hm_solve_host", "hm_farfield", "hm_matvec", "hm_query", "hm_last_error", "hm_destroy",
+           "hm_get_nodes_host", "hm_get_near_pairs_host", "hm_get_near_block_host", "hm_entries_host",
+           "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host")
+
+
+class hm_params(ctypes.Structure):
+    _fields_ = [("k0", ctypes.c_double), ("formulation", ctypes.c_int), ("leaf", ctypes.c_int),
+                ("eta", ctypes.c_double), ("aca_tol", ctypes.c_double), ("near_delta", ctypes.c_double),
+                ("aca_max_rank", ctypes.c_int), ("precision", ctypes.c_int), ("keep_matrix", ctypes.c_int)]
+
+
+class hm_body(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("m", ctypes.c_int), ("center", ctypes.c_double * 3),
+                ("semi_axes", ctypes.c_double * 3), ("rot", ctypes.c_double * 9)]
+
+
+class HmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=SO):
+    """Load libhm.so (raises when it is missing: build it with paper_2408_17116_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libhm.so not built (%s); run paper_2408_17116_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.hm_version.restype = ctypes.c_char_p
+    L.hm_last_error.restype = ctypes.c_char_p
+    L.hm_last_error.argtypes = [P]
+    L.hm_create.argtypes = [ctypes.POINTER(P), P]
+    L.hm_build_geometry.argtypes = [P, ctypes.POINTER(hm_body), I, I, ctypes.POINTER(hm_params)]
+    L.hm_fill.argtypes = [P]
+    L.hm_factor.argtypes = [P]
+    L.hm_solve.argtypes = [P, I, P, P, P]
+    L.hm_solve_host.argtypes = [P, I, P, P, P]
+    L.hm_farfield.argtypes = [P, I, P, I, P, P, P]
+    L.hm_matvec.argtypes = [P, I, P, P]
+    L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
+    L.hm_destroy.argtypes = [P]
+    L.hm_destroy.restype = None
+    L.hm_get_nodes_host.argtypes = [P, P]
+    L.hm_get_near_pairs_host.argtypes = [P, P]
+    L.hm_get_near_block_host.argtypes = [P, I, I, P]
+    L.hm_entries_host.argtypes = [P, I, P, P, P]
+    L.hm_get_perm_host.argtypes = [P, P]
+    L.hm_get_blocks_host.argtypes = [P, ctypes.POINTER(I), P]
+    L.hm_get_block_dense_host.argtypes = [P, I, P]
+    for name in EXPORTS:
+        if name not in ("hm_version", "hm_last_error", "hm_destroy"):
+            getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_bodies(bodies, ms):
+    bodies = np.asarray(bodies, dtype=np.float64).reshape(-1, 15)
+    arr = (hm_body * bodies.shape[0])()
+    for i, b in enumerate(bodies):
+        arr[i].family = 0
+        arr[i].m = int(ms[i])
+        for d in range(3):
+            arr[i].center[d] = b[d]
+            arr[i].semi_axes[d] = b[3 + d]
+        for d in range(9):
+            arr[i].rot[d] = b[6 + d]
+    return arr
+
+
+class Solver:
+    """One hm_handle.  Methods mirror the C entry points of include/hm.h."""
+
+    def __init__(self, stream=None):
+        import torch
+        self.torch = torch
+        self.L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.h = ctypes.c_void_p()
+        self._check(self.L.hm_create(ctypes.byref(self.h), ctypes.c_void_p(stream)), nohandle=True)
+
+    def _check(self, st, nohandle=False):
+        if st != HM_OK:
+            msg = "" if nohandle else self.L.hm_last_error(self.h).decode()
+            raise HmError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def hm_build_geometry(self, bodies, ms, nc, k0, leaf, eta, aca_tol, near_delta=0.5, aca_max_rank=0,
+                          keep_matrix=False):
+        self._bodies = make_bodies(bodies, ms)
+        p = hm_params(k0=float(k0), formulation=0, leaf=int(leaf), eta=float(eta), aca_tol=float(aca_tol),
+                      near_delta=float(near_delta), aca_max_rank=int(aca_max_rank), precision=0,
+                      keep_matrix=int(bool(keep_matrix)))
+        self._check(self.L.hm_build_geometry(self.h, self._bodies, len(ms), int(nc), ctypes.byref(p)))
+        self.N = int(self.hm_query("N"))
+        self.nnode = self.N // 2
+        self.nc = int(nc)
+
+    def hm_fill(self):
+        self._check(self.L.hm_fill(self.h))
+
+    def hm_factor(self):
+        self._check(self.L.hm_factor(self.h))
+
+    def hm_solve(self, kdirs, pols, out=None):
+        kd = np.ascontiguousarray(np.asarray(kdirs, np.float64).reshape(-1, 3))
+        po = np.ascontiguousarray(np.asarray(pols, np.float64).reshape(-1, 3))
+        if out is None:
+            out = self.torch.empty((kd.shape[0], self.N), dtype=self.torch.complex128, device="cuda")
+        self._check(self.L.hm_solve(self.h, kd.shape[0], _np_ptr(kd), _np_ptr(po), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def hm_solve_host(self, kdirs, pols, out=None):
+        kd = np.ascontiguousarray(np.asarray(kdirs, np.float64).reshape(-1, 3))
+        po = np.ascontiguousarray(np.asarray(pols, np.float64).reshape(-1, 3))
+        if out is None:
+            out = np.empty((kd.shape[0], self.N), dtype=np.complex128)
+        self._check(self.L.hm_solve_host(self.h, kd.shape[0], _np_ptr(kd), _np_ptr(po), _np_ptr(out)))
+        return out
+
+    def hm_farfield(self, x, dirs, want_efar=True):
+        d = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
+        x = x.reshape(-1, self.N)
+        nrhs = x.shape[0]
+        efar = self.torch.empty((nrhs, d.shape[0], 3), dtype=self.torch.complex128, device="cuda") if want_efar else None
+        rcs = np.empty((nrhs, d.shape[0]))
+        self._check(self.L.hm_farfield(self.h, nrhs, ctypes.c_void_p(x.data_ptr()), d.shape[0], _np_ptr(d),
+                                       ctypes.c_void_p(efar.data_ptr() if efar is not None else 0), _np_ptr(rcs)))
+        return efar, rcs
+
+    def hm_matvec(self, x):
+        x = x.reshape(-1, self.N).contiguous()
+        y = self.torch.empty_like(x)
+        self._check(self.L.hm_matvec(self.h, x.shape[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def hm_query(self, key):
+        out = ctypes.c_double()
+        self._check(self.L.hm_query(self.h, Q[key] if isinstance(key, str) else int(key), ctypes.byref(out)))
+        return out.value
+
+    def nodes(self):
+        t = np.empty((self.nnode, 14))
+        self._check(self.L.hm_get_nodes_host(self.h, _np_ptr(t)))
+        return t
+
+    def near_pairs(self):
+        n = int(self.hm_query("NEAR_PAIRS"))
+        out = np.empty((n, 2), dtype=np.int32)
+        self._check(self.L.hm_get_near_pairs_host(self.h, _np_ptr(out)))
+        return out
+
+    def near_block(self, tn, p):
+        out = np.empty((4, self.nc * self.nc), dtype=np.complex128)
+        self._check(self.L.hm_get_near_block_host(self.h, int(tn), int(p), _np_ptr(out)))
+        return out
+
+    def entries(self, rows, cols):
+        r = np.ascontiguousarray(np.asarray(rows, np.int32))
+        c = np.ascontiguousarray(np.asarray(cols, np.int32))
+        out = np.empty(r.size, dtype=np.complex128)
+        self._check(self.L.hm_entries_host(self.h, r.size, _np_ptr(r), _np_ptr(c), _np_ptr(out)))
+        return out
+
+    def perm(self):
+        out = np.empty(self.N, dtype=np.int32)
+        self._check(self.L.hm_get_perm_host(self.h, _np_ptr(out)))
+        return out
+
+    def blocks(self):
+        n = ctypes.c_int()
+        self._check(self.L.hm_get_blocks_host(self.h, ctypes.byref(n), None))
+        out = np.empty((n.value, 6), dtype=np.int32)
+        self._check(self.L.hm_get_blocks_host(self.h, ctypes.byref(n), _np_ptr(out)))
+        return out
+
+    def block_dense(self, b):
+        info = self.blocks()[b]
+        out = np.empty((info[4], info[2]), dtype=np.complex128)  # column-major nr x nc -> (nc, nr) C-order
+        self._check(self.L.hm_get_block_dense_host(self.h, int(b), _np_ptr(out)))
+        return out.T
