@@ -157,8 +157,12 @@ def wl_N(wl):
     return 2 * 6 * int(np.sum(np.asarray(wl["ms"]) ** 2)) * wl["nc"] ** 2
 
 
-def one_step(s, wl, dirs, host=False):
-    s.hm_build_geometry(wl["bodies"], wl["ms"], wl["nc"], wl["k"], wl["leaf"], wl["eta"], wl["aca_tol"])
+PRECISION = {"fp32r": 1, "fp64": 0}
+
+
+def one_step(s, wl, dirs, host=False, precision="fp32r"):
+    s.hm_build_geometry(wl["bodies"], wl["ms"], wl["nc"], wl["k"], wl["leaf"], wl["eta"], wl["aca_tol"],
+                        precision=PRECISION[precision])
     s.hm_fill()
     s.hm_factor()
     if host:
@@ -180,6 +184,9 @@ def main():
     ap.add_argument("--workload", default="sphere_d8_m4_nc10")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32r", choices=sorted(PRECISION),
+                    help="fp32r: FP32 H-LU + FP64 refinement (default); fp64: the plain FP64 H-LU")
+    ap.add_argument("--no-compare", action="store_true", help="skip the one-step run of the other precision")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -209,8 +216,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    prec = args.precision
     for _ in range(args.warmup):
-        one_step(s, wl, dirs)
+        one_step(s, wl, dirs, precision=prec)
     barrier()
     L0 = s.hm_query("LAUNCHES")
     clk = ClockSampler(local)
@@ -221,7 +229,7 @@ def main():
     barrier()
     ev0.record(stream)
     for _ in range(args.steps):
-        x, rcs = one_step(s, wl, dirs)
+        x, rcs = one_step(s, wl, dirs, precision=prec)
         for k in phases:
             phases[k] += s.hm_query(k)
         near_pts += s.hm_query("NEAR_QPOINTS")
@@ -237,11 +245,12 @@ def main():
     N = s.N
     value = N * world / (ms / 1000.0)
     stats = {k.lower(): s.hm_query(k) for k in ("CR", "MAX_RANK", "MEAN_RANK", "LR_BLOCKS", "DENSE_BLOCKS",
-                                                 "NEAR_PAIRS", "ACA_NONCONV", "FLOPS_FACTOR")}
+                                                 "NEAR_PAIRS", "ACA_NONCONV", "FLOPS_FACTOR", "REFINE_ITERS",
+                                                 "REFINE_RES", "STORAGE", "STORAGE32")}
     # e2e: host buffers in and out, wall clock around the public API calls
     barrier()
     t = time.perf_counter()
-    xh, rcs_h = one_step(s, wl, dirs, host=True)
+    xh, rcs_h = one_step(s, wl, dirs, host=True, precision=prec)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t
     nrhs = wl["kdirs"].shape[0]
@@ -256,14 +265,30 @@ def main():
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f64 fill; c64 H-LU + f64 refinement" if prec == "fp32r" else "f64",
+           "data": "synthetic",
            "config": {"workload": args.workload, "unknowns": N, "rhs": nrhs, "leaf": wl["leaf"], "eta": wl["eta"],
-                      "aca_tol": wl["aca_tol"], "parallelism": "replicas" if world > 1 else "single",
+                      "aca_tol": wl["aca_tol"], "precision": prec,
+                      "parallelism": "replicas" if world > 1 else "single",
                       "l2": "working set (H-matrix, near store) > L2 between steps"},
            "phases_s": per, "stats": stats, "gpu_launches": launches, "clocks": clocks,
            "e2e": {"value": N / e2e_s, "unit": "unknowns/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "wall_s": e2e_s},
            "roofline": roof}
+    if not args.no_compare:
+        # the other precision on the same GPU: one untimed warm-up step, one step timed
+        other = "fp64" if prec == "fp32r" else "fp32r"
+        one_step(s, wl, dirs, precision=other)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step(s, wl, dirs, precision=other)
+        e1.record(stream)
+        barrier()
+        cms = e0.elapsed_time(e1)
+        out["compare"] = {"precision": other, "value": N / (cms / 1000.0), "ms_per_step": cms, "steps": 1,
+                          "phases_s": {k: s.hm_query(k) for k in phases},
+                          "refine_iters": s.hm_query("REFINE_ITERS")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:

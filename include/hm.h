@@ -50,7 +50,14 @@ typedef enum {
 } hm_status;
 
 typedef enum { HM_PEC_MFIE = 0 } hm_formulation;
-typedef enum { HM_FP64 = 0 } hm_precision;
+/* HM_FP64: the plain FP64 method (complex128 H-matrix, FP64 H-LU and H-solve).
+ * HM_FP32_REFINED: the same FP64 fill; hm_factor builds a complex64 copy of the
+ * H-matrix and factors it by H-LU in FP32 (truncation tolerance factor_tol); hm_solve
+ * uses that factor as a preconditioner inside FP64 iterative refinement, with the
+ * residual b - A x taken with the FP64 H-matrix, until the relative residual is at
+ * most refine_tol.  The paper has no FP32 mode; this is the GB300-side choice that
+ * keeps FP64 only in the fill and the residual. */
+typedef enum { HM_FP64 = 0, HM_FP32_REFINED = 1 } hm_precision;
 
 /* Solver parameters.  Paper: eta and n_leaf (Sec. III, Eq. 21 and the text that
  * follows it), ACA tolerance (Sec. IV), wavenumber from the wavelength. */
@@ -64,6 +71,9 @@ typedef struct {
     int aca_max_rank;     /* ACA rank bound before a block is split (0 = 160) */
     int precision;        /* hm_precision */
     int keep_matrix;      /* nonzero: keep an unfactored copy for hm_matvec after hm_factor */
+    double factor_tol;    /* HM_FP32_REFINED: truncation tolerance of the FP32 H-LU (0 = 1e-5) */
+    double refine_tol;    /* HM_FP32_REFINED: target relative residual per RHS (0 = 1e-10) */
+    int refine_max_iter;  /* HM_FP32_REFINED: refinement step limit (0 = 30) */
 } hm_params;
 
 /* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,
@@ -99,7 +109,11 @@ enum {
     HM_Q_NEAR_QPOINTS = 18,/* kernel evaluations performed by the near-field quadrature */
     HM_Q_MEAN_RANK = 19,
     HM_Q_STORAGE_FACTOR = 20,/* complex words of the factored H-matrix */
-    HM_Q_T_RECOMPRESS = 21 /* seconds in the QR+SVD recompression after ACA */
+    HM_Q_T_RECOMPRESS = 21,/* seconds in the QR+SVD recompression after ACA */
+    HM_Q_REFINE_ITERS = 22,/* refinement steps of the last hm_solve (HM_FP32_REFINED; 0 otherwise) */
+    HM_Q_REFINE_RES = 23,  /* largest relative residual |b - A x| / |b| (FP64 H-matrix) after the last
+                              hm_solve in HM_FP32_REFINED mode */
+    HM_Q_STORAGE32 = 24    /* complex64 words of the FP32 factor (HM_FP32_REFINED) */
 };
 
 const char *hm_version(void);
@@ -122,14 +136,19 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
  * retried; on the leaf level it is stored dense. */
 hm_status hm_fill(hm_handle h);
 
-/* H-LU factorisation in place (Sec. III, Eq. 23), partial pivoting inside the
- * diagonal dense leaves. */
+/* H-LU factorisation (Sec. III, Eq. 23), partial pivoting inside the diagonal
+ * dense leaves.  HM_FP64: in place.  HM_FP32_REFINED: on a complex64 copy; the FP64
+ * H-matrix is kept for the refinement residual (and hm_matvec). */
 hm_status hm_factor(hm_handle h);
 
 /* Solve for nrhs plane waves E = pol exp(-jk khat.r): right-hand sides of Eq. 22
  * (b1 = -a_v.H_inc, b2 = a_u.H_inc), H-forward substitution (Eqs. 24, 26, 27) and
  * back substitution (Eqs. 25, 28).  inc_dirs, pols: host [nrhs][3] unit vectors.
- * x_dev: device complex128 [nrhs][N], natural unknown order. */
+ * x_dev: device complex128 [nrhs][N], natural unknown order.  In HM_FP32_REFINED mode
+ * the substitutions run with the FP32 factor inside FP64 iterative refinement;
+ * HM_ERR_NOT_CONVERGED (x_dev still holds the last iterate) when refine_tol is not
+ * reached within refine_max_iter steps.  Synchronises in HM_FP32_REFINED mode (the
+ * residual norms decide the next step on the host). */
 hm_status hm_solve(hm_handle h, int nrhs, const double *inc_dirs, const double *pols, void *x_dev);
 
 /* As hm_solve with host buffers: x_host receives complex128 [nrhs][N].  Copies in and

@@ -6,7 +6,7 @@
 
 #include "hm_internal.h"
 
-#define HM_VERSION "hm-cbie-gb300 0.1 (MFIE, FP64 H-LU)"
+#define HM_VERSION "hm-cbie-gb300 0.2 (MFIE; FP64 H-LU or FP32 H-LU + FP64 refinement)"
 #define HM_DEFAULT_RANK_CAP 160
 
 void *dalloc(hm_handle_s *h, size_t bytes)
@@ -87,6 +87,8 @@ void free_matrix(hm_handle_s *h)
     }
     free_tree(h, h->copy_blocks);
     h->copy_root = nullptr;
+    free_tree(h, h->blocks32);
+    h->root32 = nullptr;
 }
 
 void free_all(hm_handle_s *h)
@@ -182,7 +184,10 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
     return guard(h, [&] {
         if (!bodies || nbodies <= 0 || !p) throw HmError{HM_ERR_ARG, "null bodies or params"};
         if (nodes_per_dir < 2 || nodes_per_dir > HM_NC_MAX) throw HmError{HM_ERR_ARG, "nodes_per_dir out of range 2..16"};
-        if (p->formulation != HM_PEC_MFIE || p->precision != HM_FP64) throw HmError{HM_ERR_ARG, "unsupported formulation/precision"};
+        if (p->formulation != HM_PEC_MFIE) throw HmError{HM_ERR_ARG, "unsupported formulation"};
+        if (p->precision != HM_FP64 && p->precision != HM_FP32_REFINED) throw HmError{HM_ERR_ARG, "unsupported precision"};
+        if (!(p->factor_tol >= 0.0) || !(p->refine_tol >= 0.0) || p->refine_max_iter < 0)
+            throw HmError{HM_ERR_ARG, "invalid refinement parameter"};
         if (!(p->k0 >= 0.0) || p->leaf < 2 || !(p->eta > 0.0) || !(p->aca_tol > 0.0) || !(p->near_delta >= 0.0))
             throw HmError{HM_ERR_ARG, "invalid parameter value"};
         long long P = 0;
@@ -197,6 +202,9 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
         free_all(h);
         h->prm = *p;
         h->tol = p->aca_tol;
+        h->factor_tol = p->factor_tol > 0.0 ? p->factor_tol : 1e-5;
+        if (h->prm.refine_tol <= 0.0) h->prm.refine_tol = 1e-10;
+        if (h->prm.refine_max_iter <= 0) h->prm.refine_max_iter = 30;
         h->nc = nodes_per_dir;
         h->nbodies = nbodies;
         h->bodies.clear();
@@ -371,16 +379,103 @@ hm_status hm_factor(hm_handle h)
 {
     return guard(h, [&] {
         if (h->state != 2) throw HmError{HM_ERR_STATE, "hm_factor requires a filled, unfactored matrix"};
+        h->flops_factor = 0;
+        if (h->prm.precision == HM_FP32_REFINED) {
+            // the FP64 H-matrix stays unfactored: it is the refinement operator
+            Timer t(h->stream);
+            free_tree(h, h->blocks32);
+            h->root32 = clone_tree<cf>(h, h->root, h->blocks32);
+            hlu_factor<cf>(h, h->root32, h->factor_tol);
+            h->t_factor = t.stop();
+            h->state = 3;
+            return;
+        }
         if (h->prm.keep_matrix) {
             free_tree(h, h->copy_blocks);
-            h->copy_root = clone_tree(h, h->root, h->copy_blocks);
+            h->copy_root = clone_tree<zc>(h, h->root, h->copy_blocks);
         }
         Timer t(h->stream);
-        h->flops_factor = 0;
-        hlu_factor(h);
+        hlu_factor<zc>(h, h->root, h->tol);
         h->t_factor = t.stop();
         h->state = 3;
     });
+}
+
+// Per-column squared 2-norms of X (rows x cols, ld = rows): out[c] = sum_i |X[i,c]|^2.
+__global__ void k_colnorm2(const zc *__restrict__ X, int rows, double *__restrict__ out)
+{
+    const zc *x = X + (size_t)blockIdx.x * rows;
+    double s = 0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) s += zabs2(x[i]);
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffff, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        out[blockIdx.x] = t;
+    }
+}
+
+// x += d (n complex values)
+__global__ void k_axpy1(const zc *__restrict__ d, zc *__restrict__ x, size_t n)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = zadd(x[i], d[i]);
+}
+
+static std::vector<double> colnorm2(hm_handle_s *h, const zc *X, int nrhs, double *d_tmp)
+{
+    k_colnorm2<<<nrhs, 256, 0, h->stream>>>(X, h->N, d_tmp);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    std::vector<double> out(nrhs);
+    HM_CUDA(cudaMemcpyAsync(out.data(), d_tmp, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h->stream));
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    return out;
+}
+
+// FP64 iterative refinement preconditioned by the FP32 H-LU factor (tree order):
+//   x_0 = 0, r_0 = b;  d = M^-1 r (FP32 H-solve);  x += d;  r = b - A x (FP64 H-matrix)
+// until max_c |r_c| / |b_c| <= refine_tol.  Returns false when the step limit is hit.
+static bool refine_solve(hm_handle_s *h, int nrhs, const zc *b, zc *x)
+{
+    const size_t n = (size_t)h->N * nrhs;
+    zc *r = (zc *)dalloc(h, sizeof(zc) * n);
+    cf *r32 = (cf *)dalloc(h, sizeof(cf) * n);
+    zc *d = (zc *)dalloc(h, sizeof(zc) * n);
+    double *d_nrm = (double *)dalloc(h, sizeof(double) * nrhs);
+    HM_CUDA(cudaMemsetAsync(x, 0, sizeof(zc) * n, h->stream));
+    HM_CUDA(cudaMemcpyAsync(r, b, sizeof(zc) * n, cudaMemcpyDeviceToDevice, h->stream));
+    std::vector<double> bn = colnorm2(h, b, nrhs, d_nrm);
+    bool ok = false;
+    int it = 0;
+    double worst = 1.0;
+    for (it = 1; it <= h->prm.refine_max_iter; ++it) {
+        convert_vec(h, r, r32, n);
+        hsolve<cf>(h, h->root32, MVT<cf>{r32, h->N, nrhs, h->N});
+        convert_vec(h, r32, d, n);
+        k_axpy1<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(d, x, n);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+        HM_CUDA(cudaMemcpyAsync(r, b, sizeof(zc) * n, cudaMemcpyDeviceToDevice, h->stream));
+        hmatvec<zc>(h, h->root, MV{x, h->N, nrhs, h->N}, MV{r, h->N, nrhs, h->N}, zmake(-1, 0), false);
+        std::vector<double> rn = colnorm2(h, r, nrhs, d_nrm);
+        worst = 0;
+        for (int c = 0; c < nrhs; ++c) worst = std::max(worst, bn[c] > 0 ? std::sqrt(rn[c] / bn[c]) : 0.0);
+        if (worst <= h->prm.refine_tol) {
+            ok = true;
+            break;
+        }
+    }
+    h->refine_iters = std::min(it, h->prm.refine_max_iter);
+    h->refine_res = worst;
+    dfree(h, r);
+    dfree(h, r32);
+    dfree(h, d);
+    dfree(h, d_nrm);
+    return ok;
 }
 
 static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double *pol, zc *x_dev)
@@ -398,11 +493,24 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
     HM_CUDA(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, h->stream));
     zc *b = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * nrhs);
     launch_rhs(h, nrhs, d_dirs, b);
-    hsolve(h, MV{b, h->N, nrhs, h->N});
-    launch_permute(h, nrhs, b, x_dev, h->d_iperm);
+    bool converged = true;
+    if (h->prm.precision == HM_FP32_REFINED) {
+        zc *x = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * nrhs);
+        converged = refine_solve(h, nrhs, b, x);
+        launch_permute(h, nrhs, x, x_dev, h->d_iperm);
+        dfree(h, x);
+    } else {
+        hsolve<zc>(h, h->root, MV{b, h->N, nrhs, h->N});
+        launch_permute(h, nrhs, b, x_dev, h->d_iperm);
+        h->refine_iters = 0;
+        h->refine_res = 0;
+    }
     dfree(h, b);
     dfree(h, d_dirs);
     h->t_solve = t.stop();  // also keeps the host vector alive until the copy is done
+    if (!converged)
+        throw HmError{HM_ERR_NOT_CONVERGED, "iterative refinement did not reach refine_tol (residual " +
+                                                std::to_string(h->refine_res) + ")"};
 }
 
 hm_status hm_solve(hm_handle h, int nrhs, const double *inc_dirs, const double *pols, void *x_dev)
@@ -445,7 +553,7 @@ hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev)
 {
     return guard(h, [&] {
         Block *A = nullptr;
-        if (h->state == 2)
+        if (h->state == 2 || (h->state == 3 && h->prm.precision == HM_FP32_REFINED))
             A = h->root;
         else if (h->state == 3 && h->copy_root)
             A = h->copy_root;
@@ -495,6 +603,17 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_NEAR_QPOINTS: *out = (double)h->near_points; break;
         case HM_Q_MEAN_RANK: *out = meank; break;
         case HM_Q_STORAGE_FACTOR: *out = words; break;
+        case HM_Q_REFINE_ITERS: *out = h->refine_iters; break;
+        case HM_Q_REFINE_RES: *out = h->refine_res; break;
+        case HM_Q_STORAGE32: {
+            double w32 = 0;
+            for (Block32 *b : h->blocks32) {
+                if (b->type == B_DENSE) w32 += (double)b->nr * b->nc;
+                if (b->type == B_LR) w32 += (double)b->k * (b->nr + b->nc);
+            }
+            *out = w32;
+            break;
+        }
         default: throw HmError{HM_ERR_ARG, "unknown query key"};
         }
     });

@@ -6,29 +6,55 @@
 #include <math.h>
 
 typedef double2 zc;  // complex128: x = re, y = im
+typedef float2 cf;   // complex64
 
+// Real type of a complex storage type.
+template <class C> struct CReal;
+template <> struct CReal<double2> { typedef double R; };
+template <> struct CReal<float2> { typedef float R; };
+
+// Complex arithmetic, generic over complex64 / complex128 storage.
 __host__ __device__ __forceinline__ zc zmake(double r, double i) { return make_double2(r, i); }
-__host__ __device__ __forceinline__ zc zadd(zc a, zc b) { return make_double2(a.x + b.x, a.y + b.y); }
-__host__ __device__ __forceinline__ zc zsub(zc a, zc b) { return make_double2(a.x - b.x, a.y - b.y); }
-__host__ __device__ __forceinline__ zc zmul(zc a, zc b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__host__ __device__ __forceinline__ zc zconj(zc a) { return make_double2(a.x, -a.y); }
-__host__ __device__ __forceinline__ zc zscale(zc a, double s) { return make_double2(a.x * s, a.y * s); }
-__host__ __device__ __forceinline__ double zabs2(zc a) { return a.x * a.x + a.y * a.y; }
-// a += b * c
-__host__ __device__ __forceinline__ zc zfma(zc b, zc c, zc a)
+template <class C>
+__host__ __device__ __forceinline__ C cmk(typename CReal<C>::R r, typename CReal<C>::R i)
 {
-    return make_double2(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
+    C c;
+    c.x = r;
+    c.y = i;
+    return c;
+}
+template <class C> __host__ __device__ __forceinline__ C zadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <class C> __host__ __device__ __forceinline__ C zsub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <class C> __host__ __device__ __forceinline__ C zmul(C a, C b)
+{
+    return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class C> __host__ __device__ __forceinline__ C zconj(C a) { return cmk<C>(a.x, -a.y); }
+template <class C> __host__ __device__ __forceinline__ C zscale(C a, typename CReal<C>::R s)
+{
+    return cmk<C>(a.x * s, a.y * s);
+}
+template <class C> __host__ __device__ __forceinline__ typename CReal<C>::R zabs2(C a) { return a.x * a.x + a.y * a.y; }
+// a += b * c
+template <class C> __host__ __device__ __forceinline__ C zfma(C b, C c, C a)
+{
+    return cmk<C>(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
 }
 // a += conj(b) * c
-__host__ __device__ __forceinline__ zc zfmac(zc b, zc c, zc a)
+template <class C> __host__ __device__ __forceinline__ C zfmac(C b, C c, C a)
 {
-    return make_double2(fma(b.x, c.x, fma(b.y, c.y, a.x)), fma(b.x, c.y, fma(-b.y, c.x, a.y)));
+    return cmk<C>(fma(b.x, c.x, fma(b.y, c.y, a.x)), fma(b.x, c.y, fma(-b.y, c.x, a.y)));
 }
-__device__ __forceinline__ zc zdiv(zc a, zc b)
+template <class C> __device__ __forceinline__ C zdiv(C a, C b)
 {
-    double s = 1.0 / (b.x * b.x + b.y * b.y);
-    return make_double2((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+    typename CReal<C>::R s = (typename CReal<C>::R)1 / (b.x * b.x + b.y * b.y);
+    return cmk<C>((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
 }
+// Conversions between the two storage precisions.
+__host__ __device__ __forceinline__ void cconv(double2 a, double2 &o) { o = a; }
+__host__ __device__ __forceinline__ void cconv(double2 a, float2 &o) { o = make_float2((float)a.x, (float)a.y); }
+__host__ __device__ __forceinline__ void cconv(float2 a, double2 &o) { o = make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ void cconv(float2 a, float2 &o) { o = a; }
 
 // One body (cube-mapped ellipsoid): r = c + M xhat, M = Rot diag(semi), Minv = M^-1.
 struct DevBody {

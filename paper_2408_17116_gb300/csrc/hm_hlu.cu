@@ -9,59 +9,63 @@
 //   S   = P2^T L22 U22                       (recursive)
 // so that A x = b is solved by y1 = L11^-1 P1 b1, y2 = L22^-1 P2 (b2 - L21 y1),
 // x2 = U22^-1 y2, x1 = U11^-1 (y1 - U12 x2).  Low-rank blocks are U V^H; every
-// low-rank sum is recompressed (QR + SVD) to the ACA tolerance.
+// low-rank sum is recompressed (QR + SVD) to the factorisation's truncation
+// tolerance.  Everything is a template over the storage precision: complex128 for
+// the FP64 method, complex64 for the FP32 factor used as a preconditioner.
 #include <algorithm>
 
 #include "hm_internal.h"
 
-static const zc ONE = {1.0, 0.0};
-static const zc ZERO = {0.0, 0.0};
-static const zc MONE = {-1.0, 0.0};
 
-static inline MV rows_of(MV X, int r0, int nr) { return MV{X.p + r0, nr, X.cols, X.ld}; }
-void flush(hm_handle_s *h, Block *b);
+template <class Z>
+static inline MVT<Z> rows_of(MVT<Z> X, int r0, int nr) { return MVT<Z>{X.p + r0, nr, X.cols, X.ld}; }
+template <class Z>
+void flush(hm_handle_s *h, BlockT<Z> *b);
 
-static zc *zalloc(hm_handle_s *h, size_t n) { return (zc *)dalloc(h, sizeof(zc) * std::max<size_t>(n, 1)); }
+template <class Z>
+static Z *zalloc(hm_handle_s *h, size_t n) { return (Z *)dalloc(h, sizeof(Z) * std::max<size_t>(n, 1)); }
 
-static void zzero(hm_handle_s *h, MV X)
+template <class Z>
+static void zzero(hm_handle_s *h, MVT<Z> X)
 {
     if (X.rows <= 0 || X.cols <= 0) return;
     if (X.ld == X.rows) {
-        HM_CUDA(cudaMemsetAsync(X.p, 0, sizeof(zc) * (size_t)X.rows * X.cols, h->stream));
+        HM_CUDA(cudaMemsetAsync(X.p, 0, sizeof(Z) * (size_t)X.rows * X.cols, h->stream));
     } else {
         for (int j = 0; j < X.cols; ++j)
-            HM_CUDA(cudaMemsetAsync(X.p + (size_t)j * X.ld, 0, sizeof(zc) * X.rows, h->stream));
+            HM_CUDA(cudaMemsetAsync(X.p + (size_t)j * X.ld, 0, sizeof(Z) * X.rows, h->stream));
     }
 }
 
 // Y += alpha op(A) X,  op = N (X rows = A.nc) or C (X rows = A.nr)
-void hmatvec(hm_handle_s *h, Block *A, MV X, MV Y, zc alpha, bool ct)
+template <class Z>
+void hmatvec(hm_handle_s *h, BlockT<Z> *A, MVT<Z> X, MVT<Z> Y, Z alpha, bool ct)
 {
     if (X.cols <= 0) return;
     if (A->pend_k) flush(h, A);
     switch (A->type) {
     case B_DENSE:
         if (!ct)
-            zgemm(h, 'N', 'N', A->nr, X.cols, A->nc, alpha, A->D, A->nr, X.p, X.ld, ONE, Y.p, Y.ld);
+            zgemm<Z>(h, 'N', 'N', A->nr, X.cols, A->nc, alpha, A->D, A->nr, X.p, X.ld, cmk<Z>(1, 0), Y.p, Y.ld);
         else
-            zgemm(h, 'C', 'N', A->nc, X.cols, A->nr, alpha, A->D, A->nr, X.p, X.ld, ONE, Y.p, Y.ld);
+            zgemm<Z>(h, 'C', 'N', A->nc, X.cols, A->nr, alpha, A->D, A->nr, X.p, X.ld, cmk<Z>(1, 0), Y.p, Y.ld);
         break;
     case B_LR: {
         if (A->k == 0) return;
-        zc *t = zalloc(h, (size_t)A->k * X.cols);
+        Z *t = zalloc<Z>(h, (size_t)A->k * X.cols);
         if (!ct) {
-            zgemm(h, 'C', 'N', A->k, X.cols, A->nc, ONE, A->V, A->nc, X.p, X.ld, ZERO, t, A->k);
-            zgemm(h, 'N', 'N', A->nr, X.cols, A->k, alpha, A->U, A->nr, t, A->k, ONE, Y.p, Y.ld);
+            zgemm<Z>(h, 'C', 'N', A->k, X.cols, A->nc, cmk<Z>(1, 0), A->V, A->nc, X.p, X.ld, cmk<Z>(0, 0), t, A->k);
+            zgemm<Z>(h, 'N', 'N', A->nr, X.cols, A->k, alpha, A->U, A->nr, t, A->k, cmk<Z>(1, 0), Y.p, Y.ld);
         } else {
-            zgemm(h, 'C', 'N', A->k, X.cols, A->nr, ONE, A->U, A->nr, X.p, X.ld, ZERO, t, A->k);
-            zgemm(h, 'N', 'N', A->nc, X.cols, A->k, alpha, A->V, A->nc, t, A->k, ONE, Y.p, Y.ld);
+            zgemm<Z>(h, 'C', 'N', A->k, X.cols, A->nr, cmk<Z>(1, 0), A->U, A->nr, X.p, X.ld, cmk<Z>(0, 0), t, A->k);
+            zgemm<Z>(h, 'N', 'N', A->nc, X.cols, A->k, alpha, A->V, A->nc, t, A->k, cmk<Z>(1, 0), Y.p, Y.ld);
         }
         dfree(h, t);
         break;
     }
     case B_HIER:
         for (int c = 0; c < 4; ++c) {
-            Block *b = A->ch[c];
+            BlockT<Z> *b = A->ch[c];
             int ro = b->r0 - A->r0, co = b->c0 - A->c0;
             if (!ct)
                 hmatvec(h, b, rows_of(X, co, b->nc), rows_of(Y, ro, b->nr), alpha, false);
@@ -73,7 +77,8 @@ void hmatvec(hm_handle_s *h, Block *A, MV X, MV Y, zc alpha, bool ct)
 }
 
 
-static void collect_pending(Block *b, std::vector<Block *> &out)
+template <class Z>
+static void collect_pending(BlockT<Z> *b, std::vector<BlockT<Z> *> &out)
 {
     if (b->type == B_HIER) {
         for (int i = 0; i < 4; ++i) collect_pending(b->ch[i], out);
@@ -84,24 +89,25 @@ static void collect_pending(Block *b, std::vector<Block *> &out)
 
 // Recompress, in one batch, every low-rank block of b's subtree that has pending
 // updates: [U | Up_1 | ...] [V | Vp_1 | ...]^H -> truncated U' V'^H.
-void flush(hm_handle_s *h, Block *b)
+template <class Z>
+void flush(hm_handle_s *h, BlockT<Z> *b)
 {
-    std::vector<Block *> list;
+    std::vector<BlockT<Z> *> list;
     collect_pending(b, list);
     if (list.empty()) return;
     std::vector<int> ranks;
-    for (Block *c : list) {
+    for (BlockT<Z> *c : list) {
         int K = c->k + c->pend_k;
-        zc *Us = zalloc(h, (size_t)c->nr * K), *Vs = zalloc(h, (size_t)c->nc * K);
+        Z *Us = zalloc<Z>(h, (size_t)c->nr * K), *Vs = zalloc<Z>(h, (size_t)c->nc * K);
         int off = 0;
         if (c->k) {
-            zcopy2d(h, MV{Us, c->nr, c->k, c->nr}, MV{c->U, c->nr, c->k, c->nr});
-            zcopy2d(h, MV{Vs, c->nc, c->k, c->nc}, MV{c->V, c->nc, c->k, c->nc});
+            zcopy2d(h, MVT<Z>{Us, c->nr, c->k, c->nr}, MVT<Z>{c->U, c->nr, c->k, c->nr});
+            zcopy2d(h, MVT<Z>{Vs, c->nc, c->k, c->nc}, MVT<Z>{c->V, c->nc, c->k, c->nc});
             off = c->k;
         }
         for (size_t i = 0; i < c->pu.size(); ++i) {
-            zcopy2d(h, MV{Us + (size_t)off * c->nr, c->nr, c->pk[i], c->nr}, MV{c->pu[i], c->nr, c->pk[i], c->nr});
-            zcopy2d(h, MV{Vs + (size_t)off * c->nc, c->nc, c->pk[i], c->nc}, MV{c->pv[i], c->nc, c->pk[i], c->nc});
+            zcopy2d(h, MVT<Z>{Us + (size_t)off * c->nr, c->nr, c->pk[i], c->nr}, MVT<Z>{c->pu[i], c->nr, c->pk[i], c->nr});
+            zcopy2d(h, MVT<Z>{Vs + (size_t)off * c->nc, c->nc, c->pk[i], c->nc}, MVT<Z>{c->pv[i], c->nc, c->pk[i], c->nc});
             off += c->pk[i];
             dfree(h, c->pu[i]);
             dfree(h, c->pv[i]);
@@ -117,25 +123,26 @@ void flush(hm_handle_s *h, Block *b)
         c->k = K;
         ranks.push_back(K);
     }
-    batched_truncate(h, list, ranks, h->tol);
+    batched_truncate(h, list, ranks, h->cur_tol);
 }
 
 // C += alpha U V^H  (U: C.nr x k, V: C.nc x k)
-static void add_lr(hm_handle_s *h, Block *C, MV U, MV V, zc alpha)
+template <class Z>
+static void add_lr(hm_handle_s *h, BlockT<Z> *C, MVT<Z> U, MVT<Z> V, Z alpha)
 {
     int k = U.cols;
     if (k <= 0) return;
     switch (C->type) {
     case B_DENSE:
-        zgemm(h, 'N', 'C', C->nr, C->nc, k, alpha, U.p, U.ld, V.p, V.ld, ONE, C->D, C->nr);
+        zgemm<Z>(h, 'N', 'C', C->nr, C->nc, k, alpha, U.p, U.ld, V.p, V.ld, cmk<Z>(1, 0), C->D, C->nr);
         break;
     case B_LR: {
         // append (alpha U) V^H to the pending updates; recompressed at the next flush
-        zc *Up = zalloc(h, (size_t)C->nr * k), *Vp = zalloc(h, (size_t)C->nc * k);
-        zcopy2d(h, MV{Up, C->nr, k, C->nr}, U);
-        zcopy2d(h, MV{Vp, C->nc, k, C->nc}, V);
+        Z *Up = zalloc<Z>(h, (size_t)C->nr * k), *Vp = zalloc<Z>(h, (size_t)C->nc * k);
+        zcopy2d(h, MVT<Z>{Up, C->nr, k, C->nr}, U);
+        zcopy2d(h, MVT<Z>{Vp, C->nc, k, C->nc}, V);
         if (alpha.x != 1.0 || alpha.y != 0.0)  // zgemm with k = 0 computes C = alpha C
-            zgemm(h, 'N', 'N', C->nr, k, 0, ZERO, nullptr, 1, nullptr, 1, alpha, Up, C->nr);
+            zgemm<Z>(h, 'N', 'N', C->nr, k, 0, cmk<Z>(0, 0), nullptr, 1, nullptr, 1, alpha, Up, C->nr);
         C->pu.push_back(Up);
         C->pv.push_back(Vp);
         C->pk.push_back(k);
@@ -145,7 +152,7 @@ static void add_lr(hm_handle_s *h, Block *C, MV U, MV V, zc alpha)
     }
     case B_HIER:
         for (int c = 0; c < 4; ++c) {
-            Block *b = C->ch[c];
+            BlockT<Z> *b = C->ch[c];
             add_lr(h, b, rows_of(U, b->r0 - C->r0, b->nr), rows_of(V, b->c0 - C->c0, b->nc), alpha);
         }
         break;
@@ -153,30 +160,31 @@ static void add_lr(hm_handle_s *h, Block *C, MV U, MV V, zc alpha)
 }
 
 // P += alpha A B into a dense view P (A.nr x B.nc)
-static void mul_dense(hm_handle_s *h, MV P, Block *A, Block *B, zc alpha)
+template <class Z>
+static void mul_dense(hm_handle_s *h, MVT<Z> P, BlockT<Z> *A, BlockT<Z> *B, Z alpha)
 {
     if (A->type == B_LR) {
         if (A->k == 0) return;
-        zc *Y = zalloc(h, (size_t)B->nc * A->k);
-        zzero(h, MV{Y, B->nc, A->k, B->nc});
-        hmatvec(h, B, MV{A->V, A->nc, A->k, A->nc}, MV{Y, B->nc, A->k, B->nc}, ONE, true);
-        zgemm(h, 'N', 'C', A->nr, B->nc, A->k, alpha, A->U, A->nr, Y, B->nc, ONE, P.p, P.ld);
+        Z *Y = zalloc<Z>(h, (size_t)B->nc * A->k);
+        zzero(h, MVT<Z>{Y, B->nc, A->k, B->nc});
+        hmatvec(h, B, MVT<Z>{A->V, A->nc, A->k, A->nc}, MVT<Z>{Y, B->nc, A->k, B->nc}, cmk<Z>(1, 0), true);
+        zgemm<Z>(h, 'N', 'C', A->nr, B->nc, A->k, alpha, A->U, A->nr, Y, B->nc, cmk<Z>(1, 0), P.p, P.ld);
         dfree(h, Y);
     } else if (B->type == B_LR) {
         if (B->k == 0) return;
-        zc *X = zalloc(h, (size_t)A->nr * B->k);
-        zzero(h, MV{X, A->nr, B->k, A->nr});
-        hmatvec(h, A, MV{B->U, B->nr, B->k, B->nr}, MV{X, A->nr, B->k, A->nr}, ONE, false);
-        zgemm(h, 'N', 'C', A->nr, B->nc, B->k, alpha, X, A->nr, B->V, B->nc, ONE, P.p, P.ld);
+        Z *X = zalloc<Z>(h, (size_t)A->nr * B->k);
+        zzero(h, MVT<Z>{X, A->nr, B->k, A->nr});
+        hmatvec(h, A, MVT<Z>{B->U, B->nr, B->k, B->nr}, MVT<Z>{X, A->nr, B->k, A->nr}, cmk<Z>(1, 0), false);
+        zgemm<Z>(h, 'N', 'C', A->nr, B->nc, B->k, alpha, X, A->nr, B->V, B->nc, cmk<Z>(1, 0), P.p, P.ld);
         dfree(h, X);
     } else if (A->type == B_DENSE && B->type == B_DENSE) {
-        zgemm(h, 'N', 'N', A->nr, B->nc, A->nc, alpha, A->D, A->nr, B->D, B->nr, ONE, P.p, P.ld);
+        zgemm<Z>(h, 'N', 'N', A->nr, B->nc, A->nc, alpha, A->D, A->nr, B->D, B->nr, cmk<Z>(1, 0), P.p, P.ld);
     } else if (A->type == B_HIER && B->type == B_HIER) {
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j)
                 for (int l = 0; l < 2; ++l) {
-                    Block *a = A->ch[2 * i + l], *b = B->ch[2 * l + j];
-                    MV Pij{P.p + (size_t)(b->c0 - B->c0) * P.ld + (a->r0 - A->r0), a->nr, b->nc, P.ld};
+                    BlockT<Z> *a = A->ch[2 * i + l], *b = B->ch[2 * l + j];
+                    MVT<Z> Pij{P.p + (size_t)(b->c0 - B->c0) * P.ld + (a->r0 - A->r0), a->nr, b->nc, P.ld};
                     mul_dense(h, Pij, a, b, alpha);
                 }
     } else {
@@ -184,14 +192,16 @@ static void mul_dense(hm_handle_s *h, MV P, Block *A, Block *B, zc alpha)
     }
 }
 
-__global__ void k_identity(zc *I, int n)
+template <class Z>
+__global__ void k_identity(Z *I, int n)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n * n) return;
-    I[idx] = zmake((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
+    I[idx] = cmk<Z>((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
 }
 
-__global__ void k_ctrans(const zc *A, int lda, int m, int n, zc *B)  // B (n x m) = A^H
+template <class Z>
+__global__ void k_ctrans(const Z *A, int lda, int m, int n, Z *B)  // B (n x m) = A^H
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)m * n) return;
@@ -200,25 +210,26 @@ __global__ void k_ctrans(const zc *A, int lda, int m, int n, zc *B)  // B (n x m
 }
 
 // C += alpha A B  (formatted)
-static void addmul(hm_handle_s *h, Block *C, Block *A, Block *B, zc alpha)
+template <class Z>
+static void addmul(hm_handle_s *h, BlockT<Z> *C, BlockT<Z> *A, BlockT<Z> *B, Z alpha)
 {
     if (A->pend_k) flush(h, A);
     if (B->pend_k) flush(h, B);
     if (A->type == B_LR) {
         if (A->k == 0) return;
-        zc *Y = zalloc(h, (size_t)B->nc * A->k);  // Y = B^H V_A
-        zzero(h, MV{Y, B->nc, A->k, B->nc});
-        hmatvec(h, B, MV{A->V, A->nc, A->k, A->nc}, MV{Y, B->nc, A->k, B->nc}, ONE, true);
-        add_lr(h, C, MV{A->U, A->nr, A->k, A->nr}, MV{Y, B->nc, A->k, B->nc}, alpha);
+        Z *Y = zalloc<Z>(h, (size_t)B->nc * A->k);  // Y = B^H V_A
+        zzero(h, MVT<Z>{Y, B->nc, A->k, B->nc});
+        hmatvec(h, B, MVT<Z>{A->V, A->nc, A->k, A->nc}, MVT<Z>{Y, B->nc, A->k, B->nc}, cmk<Z>(1, 0), true);
+        add_lr(h, C, MVT<Z>{A->U, A->nr, A->k, A->nr}, MVT<Z>{Y, B->nc, A->k, B->nc}, alpha);
         dfree(h, Y);
         return;
     }
     if (B->type == B_LR) {
         if (B->k == 0) return;
-        zc *X = zalloc(h, (size_t)A->nr * B->k);  // X = A U_B
-        zzero(h, MV{X, A->nr, B->k, A->nr});
-        hmatvec(h, A, MV{B->U, B->nr, B->k, B->nr}, MV{X, A->nr, B->k, A->nr}, ONE, false);
-        add_lr(h, C, MV{X, A->nr, B->k, A->nr}, MV{B->V, B->nc, B->k, B->nc}, alpha);
+        Z *X = zalloc<Z>(h, (size_t)A->nr * B->k);  // X = A U_B
+        zzero(h, MVT<Z>{X, A->nr, B->k, A->nr});
+        hmatvec(h, A, MVT<Z>{B->U, B->nr, B->k, B->nr}, MVT<Z>{X, A->nr, B->k, A->nr}, cmk<Z>(1, 0), false);
+        add_lr(h, C, MVT<Z>{X, A->nr, B->k, A->nr}, MVT<Z>{B->V, B->nc, B->k, B->nc}, alpha);
         dfree(h, X);
         return;
     }
@@ -229,28 +240,28 @@ static void addmul(hm_handle_s *h, Block *C, Block *A, Block *B, zc alpha)
         return;
     }
     if (C->type == B_DENSE) {
-        mul_dense(h, MV{C->D, C->nr, C->nc, C->nr}, A, B, alpha);
+        mul_dense(h, MVT<Z>{C->D, C->nr, C->nc, C->nr}, A, B, alpha);
         return;
     }
     if (C->type == B_LR) {
         if (A->type == B_DENSE && B->type == B_DENSE) {
             // A B = A (B^H)^H: exact low-rank form of rank A.nc
-            zc *Bh = zalloc(h, (size_t)B->nc * B->nr);
+            Z *Bh = zalloc<Z>(h, (size_t)B->nc * B->nr);
             size_t n = (size_t)B->nr * B->nc;
-            k_ctrans<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(B->D, B->nr, B->nr, B->nc, Bh);
+            k_ctrans<Z><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(B->D, B->nr, B->nr, B->nc, Bh);
             HM_CHECK_LAUNCH();
             count_launch(h);
-            add_lr(h, C, MV{A->D, A->nr, A->nc, A->nr}, MV{Bh, B->nc, B->nr, B->nc}, alpha);
+            add_lr(h, C, MVT<Z>{A->D, A->nr, A->nc, A->nr}, MVT<Z>{Bh, B->nc, B->nr, B->nc}, alpha);
             dfree(h, Bh);
             return;
         }
         if (A->type == B_HIER && B->type == B_HIER) {
             // hierarchical product into a low-rank block: products of the 2 x 2 children into
             // temporary low-rank blocks, agglomerated and recompressed into C
-            Block T[4];
+            BlockT<Z> T[4];
             for (int i = 0; i < 2; ++i)
                 for (int j = 0; j < 2; ++j) {
-                    Block &t = T[2 * i + j];
+                    BlockT<Z> &t = T[2 * i + j];
                     t.type = B_LR;
                     t.r0 = A->ch[2 * i]->r0;
                     t.nr = A->ch[2 * i]->nr;
@@ -260,29 +271,29 @@ static void addmul(hm_handle_s *h, Block *C, Block *A, Block *B, zc alpha)
                 }
             for (int i = 0; i < 2; ++i)
                 for (int j = 0; j < 2; ++j)
-                    for (int l = 0; l < 2; ++l) addmul(h, &T[2 * i + j], A->ch[2 * i + l], B->ch[2 * l + j], ONE);
+                    for (int l = 0; l < 2; ++l) addmul(h, &T[2 * i + j], A->ch[2 * i + l], B->ch[2 * l + j], cmk<Z>(1, 0));
             {
                 // recompress the four temporaries in one batch
-                Block Hh;
+                BlockT<Z> Hh;
                 Hh.type = B_HIER;
                 for (int t = 0; t < 4; ++t) Hh.ch[t] = &T[t];
                 flush(h, &Hh);
             }
             int K = T[0].k + T[1].k + T[2].k + T[3].k;
             if (K > 0) {
-                zc *Ua = zalloc(h, (size_t)C->nr * K), *Va = zalloc(h, (size_t)C->nc * K);
-                zzero(h, MV{Ua, C->nr, K, C->nr});
-                zzero(h, MV{Va, C->nc, K, C->nc});
+                Z *Ua = zalloc<Z>(h, (size_t)C->nr * K), *Va = zalloc<Z>(h, (size_t)C->nc * K);
+                zzero(h, MVT<Z>{Ua, C->nr, K, C->nr});
+                zzero(h, MVT<Z>{Va, C->nc, K, C->nc});
                 int off = 0;
                 for (int t = 0; t < 4; ++t) {
                     if (!T[t].k) continue;
-                    zcopy2d(h, MV{Ua + (size_t)off * C->nr + (T[t].r0 - C->r0), T[t].nr, T[t].k, C->nr},
-                            MV{T[t].U, T[t].nr, T[t].k, T[t].nr});
-                    zcopy2d(h, MV{Va + (size_t)off * C->nc + (T[t].c0 - C->c0), T[t].nc, T[t].k, C->nc},
-                            MV{T[t].V, T[t].nc, T[t].k, T[t].nc});
+                    zcopy2d(h, MVT<Z>{Ua + (size_t)off * C->nr + (T[t].r0 - C->r0), T[t].nr, T[t].k, C->nr},
+                            MVT<Z>{T[t].U, T[t].nr, T[t].k, T[t].nr});
+                    zcopy2d(h, MVT<Z>{Va + (size_t)off * C->nc + (T[t].c0 - C->c0), T[t].nc, T[t].k, C->nc},
+                            MVT<Z>{T[t].V, T[t].nc, T[t].k, T[t].nc});
                     off += T[t].k;
                 }
-                add_lr(h, C, MV{Ua, C->nr, K, C->nr}, MV{Va, C->nc, K, C->nc}, alpha);
+                add_lr(h, C, MVT<Z>{Ua, C->nr, K, C->nr}, MVT<Z>{Va, C->nc, K, C->nc}, alpha);
                 dfree(h, Ua);
                 dfree(h, Va);
             }
@@ -294,15 +305,15 @@ static void addmul(hm_handle_s *h, Block *C, Block *A, Block *B, zc alpha)
         }
         // a dense operand at a hierarchical level (a block stored dense after ACA hit its
         // rank bound): dense product, then [U | P][V | I]
-        zc *P = zalloc(h, (size_t)C->nr * C->nc);
-        zzero(h, MV{P, C->nr, C->nc, C->nr});
-        mul_dense(h, MV{P, C->nr, C->nc, C->nr}, A, B, ONE);
-        zc *I = zalloc(h, (size_t)C->nc * C->nc);
+        Z *P = zalloc<Z>(h, (size_t)C->nr * C->nc);
+        zzero(h, MVT<Z>{P, C->nr, C->nc, C->nr});
+        mul_dense(h, MVT<Z>{P, C->nr, C->nc, C->nr}, A, B, cmk<Z>(1, 0));
+        Z *I = zalloc<Z>(h, (size_t)C->nc * C->nc);
         size_t n = (size_t)C->nc * C->nc;
-        k_identity<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(I, C->nc);
+        k_identity<Z><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(I, C->nc);
         HM_CHECK_LAUNCH();
         count_launch(h);
-        add_lr(h, C, MV{P, C->nr, C->nc, C->nr}, MV{I, C->nc, C->nc, C->nc}, alpha);
+        add_lr(h, C, MVT<Z>{P, C->nr, C->nc, C->nr}, MVT<Z>{I, C->nc, C->nc, C->nc}, alpha);
         dfree(h, P);
         dfree(h, I);
         return;
@@ -311,7 +322,8 @@ static void addmul(hm_handle_s *h, Block *C, Block *A, Block *B, zc alpha)
 }
 
 // X <- L^-1 P X for a factored diagonal block L (rows of X = L.nr)
-static void trsm_L_mv(hm_handle_s *h, Block *L, MV X)
+template <class Z>
+static void trsm_L_mv(hm_handle_s *h, BlockT<Z> *L, MVT<Z> X)
 {
     if (X.cols <= 0) return;
     if (L->type == B_DENSE) {
@@ -319,85 +331,88 @@ static void trsm_L_mv(hm_handle_s *h, Block *L, MV X)
         ztrsm_lln(h, L->D, L->nr, L->nr, X);
         return;
     }
-    Block *L11 = L->ch[0], *L21 = L->ch[2], *L22 = L->ch[3];
-    MV X1 = rows_of(X, 0, L11->nr), X2 = rows_of(X, L11->nr, L22->nr);
+    BlockT<Z> *L11 = L->ch[0], *L21 = L->ch[2], *L22 = L->ch[3];
+    MVT<Z> X1 = rows_of(X, 0, L11->nr), X2 = rows_of(X, L11->nr, L22->nr);
     trsm_L_mv(h, L11, X1);
-    hmatvec(h, L21, X1, X2, MONE, false);
+    hmatvec(h, L21, X1, X2, cmk<Z>(-1, 0), false);
     trsm_L_mv(h, L22, X2);
 }
 
 // X <- U^-1 X
-static void trsm_U_mv(hm_handle_s *h, Block *U, MV X)
+template <class Z>
+static void trsm_U_mv(hm_handle_s *h, BlockT<Z> *U, MVT<Z> X)
 {
     if (X.cols <= 0) return;
     if (U->type == B_DENSE) {
         ztrsm_lun(h, U->D, U->nr, U->nr, X);
         return;
     }
-    Block *U11 = U->ch[0], *U12 = U->ch[1], *U22 = U->ch[3];
-    MV X1 = rows_of(X, 0, U11->nr), X2 = rows_of(X, U11->nr, U22->nr);
+    BlockT<Z> *U11 = U->ch[0], *U12 = U->ch[1], *U22 = U->ch[3];
+    MVT<Z> X1 = rows_of(X, 0, U11->nr), X2 = rows_of(X, U11->nr, U22->nr);
     trsm_U_mv(h, U22, X2);
-    hmatvec(h, U12, X2, X1, MONE, false);
+    hmatvec(h, U12, X2, X1, cmk<Z>(-1, 0), false);
     trsm_U_mv(h, U11, X1);
 }
 
 // X <- U^-H X
-static void trsm_UH_mv(hm_handle_s *h, Block *U, MV X)
+template <class Z>
+static void trsm_UH_mv(hm_handle_s *h, BlockT<Z> *U, MVT<Z> X)
 {
     if (X.cols <= 0) return;
     if (U->type == B_DENSE) {
         ztrsm_luh(h, U->D, U->nr, U->nr, X);
         return;
     }
-    Block *U11 = U->ch[0], *U12 = U->ch[1], *U22 = U->ch[3];
-    MV X1 = rows_of(X, 0, U11->nr), X2 = rows_of(X, U11->nr, U22->nr);
+    BlockT<Z> *U11 = U->ch[0], *U12 = U->ch[1], *U22 = U->ch[3];
+    MVT<Z> X1 = rows_of(X, 0, U11->nr), X2 = rows_of(X, U11->nr, U22->nr);
     trsm_UH_mv(h, U11, X1);
-    hmatvec(h, U12, X1, X2, MONE, true);
+    hmatvec(h, U12, X1, X2, cmk<Z>(-1, 0), true);
     trsm_UH_mv(h, U22, X2);
 }
 
-static void trsm_UH_mv(hm_handle_s *h, Block *U, MV X);
 
 // B <- L^-1 P B  (B has the row cluster of L)
-static void trsm_L_block(hm_handle_s *h, Block *L, Block *B)
+template <class Z>
+static void trsm_L_block(hm_handle_s *h, BlockT<Z> *L, BlockT<Z> *B)
 {
     flush(h, B);
     if (B->type == B_LR) {
-        trsm_L_mv(h, L, MV{B->U, B->nr, B->k, B->nr});
+        trsm_L_mv(h, L, MVT<Z>{B->U, B->nr, B->k, B->nr});
         return;
     }
     if (B->type == B_DENSE) {
-        trsm_L_mv(h, L, MV{B->D, B->nr, B->nc, B->nr});
+        trsm_L_mv(h, L, MVT<Z>{B->D, B->nr, B->nc, B->nr});
         return;
     }
     if (L->type != B_HIER) throw HmError{HM_ERR_STATE, "trsm_L_block: hierarchical B under a dense L"};
     for (int j = 0; j < 2; ++j) {
         trsm_L_block(h, L->ch[0], B->ch[j]);
-        addmul(h, B->ch[2 + j], L->ch[2], B->ch[j], MONE);
+        addmul(h, B->ch[2 + j], L->ch[2], B->ch[j], cmk<Z>(-1, 0));
         trsm_L_block(h, L->ch[3], B->ch[2 + j]);
     }
 }
 
 // B <- B U^-1  (B has the column cluster of U)
-static void trsm_U_right_block(hm_handle_s *h, Block *U, Block *B)
+template <class Z>
+static void trsm_U_right_block(hm_handle_s *h, BlockT<Z> *U, BlockT<Z> *B)
 {
     flush(h, B);
     if (B->type == B_LR) {
-        trsm_UH_mv(h, U, MV{B->V, B->nc, B->k, B->nc});
+        trsm_UH_mv(h, U, MVT<Z>{B->V, B->nc, B->k, B->nc});
         return;
     }
     if (B->type == B_DENSE) {
         if (U->type == B_DENSE) {
-            ztrsm_run(h, U->D, U->nr, U->nr, MV{B->D, B->nr, B->nc, B->nr});
+            ztrsm_run(h, U->D, U->nr, U->nr, MVT<Z>{B->D, B->nr, B->nc, B->nr});
             return;
         }
         // B U^-1 = (U^-H B^H)^H
-        zc *Bh = zalloc(h, (size_t)B->nc * B->nr);
+        Z *Bh = zalloc<Z>(h, (size_t)B->nc * B->nr);
         size_t n = (size_t)B->nr * B->nc;
-        k_ctrans<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(B->D, B->nr, B->nr, B->nc, Bh);
+        k_ctrans<Z><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(B->D, B->nr, B->nr, B->nc, Bh);
         HM_CHECK_LAUNCH();
-        trsm_UH_mv(h, U, MV{Bh, B->nc, B->nr, B->nc});
-        k_ctrans<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(Bh, B->nc, B->nc, B->nr, B->D);
+        trsm_UH_mv(h, U, MVT<Z>{Bh, B->nc, B->nr, B->nc});
+        k_ctrans<Z><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(Bh, B->nc, B->nc, B->nr, B->D);
         HM_CHECK_LAUNCH();
         count_launch(h, 2);
         dfree(h, Bh);
@@ -406,12 +421,13 @@ static void trsm_U_right_block(hm_handle_s *h, Block *U, Block *B)
     if (U->type != B_HIER) throw HmError{HM_ERR_STATE, "trsm_U_right_block: hierarchical B under a dense U"};
     for (int i = 0; i < 2; ++i) {
         trsm_U_right_block(h, U->ch[0], B->ch[2 * i]);
-        addmul(h, B->ch[2 * i + 1], B->ch[2 * i], U->ch[1], MONE);
+        addmul(h, B->ch[2 * i + 1], B->ch[2 * i], U->ch[1], cmk<Z>(-1, 0));
         trsm_U_right_block(h, U->ch[3], B->ch[2 * i + 1]);
     }
 }
 
-static void hlu_rec(hm_handle_s *h, Block *A, int *d_info)
+template <class Z>
+static void hlu_rec(hm_handle_s *h, BlockT<Z> *A, int *d_info)
 {
     flush(h, A);
     if (A->type == B_DENSE) {
@@ -423,62 +439,106 @@ static void hlu_rec(hm_handle_s *h, Block *A, int *d_info)
     hlu_rec(h, A->ch[0], d_info);
     trsm_L_block(h, A->ch[0], A->ch[1]);
     trsm_U_right_block(h, A->ch[0], A->ch[2]);
-    addmul(h, A->ch[3], A->ch[2], A->ch[1], MONE);
+    addmul(h, A->ch[3], A->ch[2], A->ch[1], cmk<Z>(-1, 0));
     hlu_rec(h, A->ch[3], d_info);
 }
 
 // Invariant: operands of addmul / hmatvec are free of pending updates (every
 // triangular solve and every diagonal step flushes its target subtree first), so
-// only low-rank leaves are checked there.
-void hlu_factor(hm_handle_s *h)
+// only low-rank leaves are checked there.  tol: truncation tolerance of every
+// recompression performed by the factorisation.
+template <class Z>
+void hlu_factor(hm_handle_s *h, BlockT<Z> *root, double tol)
 {
+    double saved = h->cur_tol;
+    h->cur_tol = tol;
     int *d_info = (int *)dalloc(h, sizeof(int));
     HM_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), h->stream));
-    hlu_rec(h, h->root, d_info);
-    flush(h, h->root);
+    hlu_rec(h, root, d_info);
+    flush(h, root);
     int info = 0;
     HM_CUDA(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     HM_CUDA(cudaStreamSynchronize(h->stream));
     dfree(h, d_info);
+    h->cur_tol = saved;
     if (info) throw HmError{HM_ERR_SINGULAR, "H-LU: zero pivot in a diagonal leaf"};
 }
 
-void hsolve(hm_handle_s *h, MV X)
+template <class Z>
+void hsolve(hm_handle_s *h, BlockT<Z> *root, MVT<Z> X)
 {
-    trsm_L_mv(h, h->root, X);
-    trsm_U_mv(h, h->root, X);
+    trsm_L_mv(h, root, X);
+    trsm_U_mv(h, root, X);
 }
 
-Block *clone_tree(hm_handle_s *h, Block *b, std::vector<Block *> &owned)
+template <class Ti, class To>
+__global__ void k_convert(const Ti *__restrict__ x, To *__restrict__ y, size_t n)
 {
-    Block *c = new Block(*b);
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cconv(x[i], y[i]);
+}
+
+template <class Ti, class To>
+void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n)
+{
+    if (n == 0) return;
+    k_convert<Ti, To><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(x, y, n);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+}
+
+template <class Z>
+BlockT<Z> *clone_tree(hm_handle_s *h, Block *b, std::vector<BlockT<Z> *> &owned)
+{
+    BlockT<Z> *c = new BlockT<Z>();
     owned.push_back(c);
-    c->piv = nullptr;
-    c->D = c->U = c->V = nullptr;
+    c->type = b->type;
+    c->r0 = b->r0;
+    c->nr = b->nr;
+    c->c0 = b->c0;
+    c->nc = b->nc;
+    c->t = b->t;
+    c->s = b->s;
+    c->k = b->k;
+    c->leaf_id = b->leaf_id;
     if (b->type == B_DENSE) {
-        c->D = zalloc(h, (size_t)b->nr * b->nc);
-        HM_CUDA(cudaMemcpyAsync(c->D, b->D, sizeof(zc) * (size_t)b->nr * b->nc, cudaMemcpyDeviceToDevice, h->stream));
+        c->D = zalloc<Z>(h, (size_t)b->nr * b->nc);
+        convert_vec(h, b->D, c->D, (size_t)b->nr * b->nc);
     } else if (b->type == B_LR) {
         if (b->k) {
-            c->U = zalloc(h, (size_t)b->nr * b->k);
-            c->V = zalloc(h, (size_t)b->nc * b->k);
-            HM_CUDA(cudaMemcpyAsync(c->U, b->U, sizeof(zc) * (size_t)b->nr * b->k, cudaMemcpyDeviceToDevice, h->stream));
-            HM_CUDA(cudaMemcpyAsync(c->V, b->V, sizeof(zc) * (size_t)b->nc * b->k, cudaMemcpyDeviceToDevice, h->stream));
+            c->U = zalloc<Z>(h, (size_t)b->nr * b->k);
+            c->V = zalloc<Z>(h, (size_t)b->nc * b->k);
+            convert_vec(h, b->U, c->U, (size_t)b->nr * b->k);
+            convert_vec(h, b->V, c->V, (size_t)b->nc * b->k);
         }
     } else {
-        for (int i = 0; i < 4; ++i) c->ch[i] = clone_tree(h, b->ch[i], owned);
+        for (int i = 0; i < 4; ++i) c->ch[i] = clone_tree<Z>(h, b->ch[i], owned);
     }
     return c;
 }
 
-void free_tree(hm_handle_s *h, std::vector<Block *> &owned)
+template <class Z>
+void free_tree(hm_handle_s *h, std::vector<BlockT<Z> *> &owned)
 {
-    for (Block *b : owned) {
+    for (BlockT<Z> *b : owned) {
         if (b->D) dfree(h, b->D);
         if (b->U) dfree(h, b->U);
         if (b->V) dfree(h, b->V);
         if (b->piv) dfree(h, b->piv);
+        for (Z *q : b->pu) dfree(h, q);
+        for (Z *q : b->pv) dfree(h, q);
         delete b;
     }
     owned.clear();
 }
+
+#define HM_INST_HLU(Z)                                                                             \
+    template void hlu_factor<Z>(hm_handle_s *, BlockT<Z> *, double);                               \
+    template void hsolve<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>);                                   \
+    template void hmatvec<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>, MVT<Z>, Z, bool);                 \
+    template BlockT<Z> *clone_tree<Z>(hm_handle_s *, Block *, std::vector<BlockT<Z> *> &);         \
+    template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);
+HM_INST_HLU(zc)
+HM_INST_HLU(cf)
+template void convert_vec<zc, cf>(hm_handle_s *, const zc *, cf *, size_t);
+template void convert_vec<cf, zc>(hm_handle_s *, const cf *, zc *, size_t);

@@ -45,27 +45,34 @@ struct Cluster {
 
 enum BType { B_DENSE = 0, B_LR = 1, B_HIER = 2 };
 
-struct Block {
+// One node of the block cluster tree; C = complex128 (the FP64 H-matrix) or
+// complex64 (the FP32 copy that is factored as a preconditioner).
+template <class C>
+struct BlockT {
     BType type = B_DENSE;
     int r0 = 0, nr = 0, c0 = 0, nc = 0;  // tree-ordered unknown ranges
     int t = -1, s = -1;                  // clusters
-    Block *ch[4] = {nullptr, nullptr, nullptr, nullptr};  // (0,0) (0,1) (1,0) (1,1)
-    zc *D = nullptr;                     // dense, column-major, ld = nr
+    BlockT *ch[4] = {nullptr, nullptr, nullptr, nullptr};  // (0,0) (0,1) (1,0) (1,1)
+    C *D = nullptr;                      // dense, column-major, ld = nr
     int *piv = nullptr;                  // diagonal dense leaf after LU (device, nr entries)
-    zc *U = nullptr, *V = nullptr;       // low rank: A = U V^H, U nr x k, V nc x k
+    C *U = nullptr, *V = nullptr;        // low rank: A = U V^H, U nr x k, V nc x k
     int k = 0;
     int leaf_id = -1;
     // low-rank updates not yet recompressed: sum_i Up_i Vp_i^H (owned buffers)
-    std::vector<zc *> pu, pv;
+    std::vector<C *> pu, pv;
     std::vector<int> pk;
     int pend_k = 0;
 };
+typedef BlockT<zc> Block;
+typedef BlockT<cf> Block32;
 
 // A dense column-major view in device memory.
-struct MV {
-    zc *p;
+template <class C>
+struct MVT {
+    C *p;
     int rows, cols, ld;
 };
+typedef MVT<zc> MV;
 
 struct hm_handle_s {
     cudaStream_t stream = nullptr;
@@ -98,6 +105,11 @@ struct hm_handle_s {
     std::vector<Block *> leaves;
     Block *copy_root = nullptr;   // unfactored copy (keep_matrix)
     std::vector<Block *> copy_blocks;
+    Block32 *root32 = nullptr;    // FP32 factor (precision HM_FP32_REFINED)
+    std::vector<Block32 *> blocks32;
+    double factor_tol = 1e-5;     // truncation tolerance of the FP32 factor
+    int refine_iters = 0;         // refinement steps taken by the last solve
+    double refine_res = 0;        // final relative residual of the last solve (max over RHS)
     // statistics
     double t_geom = 0, t_near = 0, t_dense = 0, t_aca = 0, t_trunc = 0, t_factor = 0, t_solve = 0;
     double flops_factor = 0;
@@ -105,6 +117,7 @@ struct hm_handle_s {
     int aca_nonconv = 0;
     unsigned long long near_points = 0;
     double tol = 1e-7;
+    double cur_tol = 1e-7;       // truncation tolerance of the factorisation in progress
 };
 
 // ---- device memory (stream-ordered pool) ----
@@ -130,23 +143,34 @@ void launch_dense_fill(hm_handle_s *h, const std::vector<DenseDesc> &descs);
 void launch_aca(hm_handle_s *h, const std::vector<LRDesc> &descs, int *d_rank, int *d_flag);
 void launch_entries(hm_handle_s *h, int n, const int *d_rows, const int *d_cols, zc *d_out);
 
-// ---- hm_linalg.cu (complex FP64 dense kernels) ----
+// ---- hm_linalg.cu (complex dense kernels, instantiated for complex128 and complex64) ----
 // C = alpha op(A) op(B) + beta C, op: 'N' or 'C' (conjugate transpose)
-void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, const zc *A, int lda,
-           const zc *B, int ldb, zc beta, zc *C, int ldc);
-void zgetrf(hm_handle_s *h, int n, zc *A, int lda, int *piv, int *d_info);
-void zlaswp(hm_handle_s *h, MV X, const int *piv, int n);  // apply piv[0..n) forward to rows
-void ztrsm_lln(hm_handle_s *h, const zc *L, int ldl, int n, MV X);   // X = L^-1 X, unit lower
-void ztrsm_lun(hm_handle_s *h, const zc *U, int ldu, int n, MV X);   // X = U^-1 X, upper
-void ztrsm_luh(hm_handle_s *h, const zc *U, int ldu, int n, MV X);   // X = U^-H X
-void ztrsm_run(hm_handle_s *h, const zc *U, int ldu, int n, MV X);   // X = X U^-1 (X rows x n)
-void zcopy2d(hm_handle_s *h, MV dst, MV src);
-void zscale_cols(hm_handle_s *h, MV X, const double *d_s);           // X[:,j] *= s[j]
+template <class C>
+void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, C alpha, const C *A, int lda, const C *B, int ldb,
+           C beta, C *Cm, int ldc);
+template <class C>
+void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info);
+template <class C>
+void zlaswp(hm_handle_s *h, MVT<C> X, const int *piv, int n);  // apply piv[0..n) forward to rows
+template <class C>
+void ztrsm_lln(hm_handle_s *h, const C *L, int ldl, int n, MVT<C> X);  // X = L^-1 X, unit lower
+template <class C>
+void ztrsm_lun(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X);  // X = U^-1 X, upper
+template <class C>
+void ztrsm_luh(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X);  // X = U^-H X
+template <class C>
+void ztrsm_run(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X);  // X = X U^-1 (X rows x n)
+template <class C>
+void zcopy2d(hm_handle_s *h, MVT<C> dst, MVT<C> src);
+template <class C>
+void zscale_cols(hm_handle_s *h, MVT<C> X, const typename CReal<C>::R *d_s);  // X[:,j] *= s[j]
 // Truncated recompression of A = U V^H (U m x K, V n x K): returns the new rank;
 // *Uo, *Vo receive freshly allocated factors (balanced: both scaled by sqrt(sigma)).
-int truncate_lr(hm_handle_s *h, int m, int n, int K, const zc *U, int ldu, const zc *V, int ldv,
-                double tol, int kmax, zc **Uo, zc **Vo);
-void batched_truncate(hm_handle_s *h, std::vector<Block *> &blks, const std::vector<int> &ranks, double tol);
+template <class C>
+int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const C *V, int ldv, double tol, int kmax,
+                C **Uo, C **Vo);
+template <class C>
+void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std::vector<int> &ranks, double tol);
 
 // ---- hm_io.cu ----
 void launch_rhs(hm_handle_s *h, int nrhs, const double *d_dirs, zc *d_b);  // tree order
@@ -154,12 +178,21 @@ void launch_permute(hm_handle_s *h, int nrhs, const zc *src, zc *dst, const int 
 void launch_farfield(hm_handle_s *h, int nrhs, const zc *d_x, int nang, const double *d_dirs, zc *d_efar,
                      double *d_rcs);
 
-// ---- hm_hlu.cpp ----
-void hlu_factor(hm_handle_s *h);
-void hsolve(hm_handle_s *h, MV X);                 // X (tree order) <- A^-1 X
-void hmatvec(hm_handle_s *h, Block *A, MV X, MV Y, zc alpha, bool conjtrans);  // Y += alpha op(A) X
-Block *clone_tree(hm_handle_s *h, Block *b, std::vector<Block *> &owned);
-void free_tree(hm_handle_s *h, std::vector<Block *> &owned);
+// ---- hm_hlu.cu (instantiated for complex128 and complex64) ----
+template <class C>
+void hlu_factor(hm_handle_s *h, BlockT<C> *root, double tol);
+template <class C>
+void hsolve(hm_handle_s *h, BlockT<C> *root, MVT<C> X);  // X (tree order) <- A^-1 X
+template <class C>
+void hmatvec(hm_handle_s *h, BlockT<C> *A, MVT<C> X, MVT<C> Y, C alpha, bool conjtrans);  // Y += alpha op(A) X
+// Deep copy of a block tree, converting the storage precision (complex128 -> C).
+template <class C>
+BlockT<C> *clone_tree(hm_handle_s *h, Block *b, std::vector<BlockT<C> *> &owned);
+template <class C>
+void free_tree(hm_handle_s *h, std::vector<BlockT<C> *> &owned);
+// y[i] = (To) x[i] for n complex values
+template <class Ti, class To>
+void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n);
 
 // ---- hm_planner.cpp ----
 void plan_geometry(hm_handle_s *h);  // nodes, near pairs, cluster tree, block tree

@@ -17,44 +17,48 @@
 #define GB_N 64
 #define GB_K 8
 
+template <class C>
 struct GemmArgs {
     int opA, opB;  // 0 'N', 1 'C'
     int m, n, k;
-    zc alpha, beta;
-    const zc *A;
+    C alpha, beta;
+    const C *A;
     int lda;
-    const zc *B;
+    const C *B;
     int ldb;
-    zc *C;
+    C *Cm;
     int ldc;
-    zc *work;      // split-K partials [splits][m][n] (column-major m x n each), or null
+    C *work;      // split-K partials [splits][m][n] (column-major m x n each), or null
     int kchunk;
 };
 
-__device__ __forceinline__ zc loadA(const GemmArgs &g, int i, int p)
+template <class C>
+__device__ __forceinline__ C loadA(const GemmArgs<C> &g, int i, int p)
 {
-    if (i >= g.m || p >= g.k) return zmake(0, 0);
+    if (i >= g.m || p >= g.k) return cmk<C>(0, 0);
     return g.opA ? zconj(g.A[(size_t)i * g.lda + p]) : g.A[(size_t)p * g.lda + i];
 }
-__device__ __forceinline__ zc loadB(const GemmArgs &g, int p, int j)
+template <class C>
+__device__ __forceinline__ C loadB(const GemmArgs<C> &g, int p, int j)
 {
-    if (j >= g.n || p >= g.k) return zmake(0, 0);
+    if (j >= g.n || p >= g.k) return cmk<C>(0, 0);
     return g.opB ? zconj(g.B[(size_t)p * g.ldb + j]) : g.B[(size_t)j * g.ldb + p];
 }
 
-__global__ void __launch_bounds__(256) k_zgemm(GemmArgs g)
+template <class C>
+__global__ void __launch_bounds__(256) k_zgemm(GemmArgs<C> g)
 {
-    __shared__ zc As[GB_K][GB_M];
-    __shared__ zc Bs[GB_K][GB_N + 1];
+    __shared__ C As[GB_K][GB_M];
+    __shared__ C Bs[GB_K][GB_N + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.x * GB_M, j0 = blockIdx.y * GB_N;
     const int kb = blockIdx.z * g.kchunk, ke = min(g.k, kb + g.kchunk);
-    zc acc[4][4];
+    C acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = zmake(0, 0);
+        for (int b = 0; b < 4; ++b) acc[a][b] = cmk<C>(0, 0);
     for (int p0 = kb; p0 < ke; p0 += GB_K) {
         // load 64 x 8 of A and 8 x 64 of B: 512 elements each, 2 per thread
 #pragma unroll
@@ -62,14 +66,14 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs g)
             int e = tid + r * 256;
             int ii = e & 63, pp = e >> 6;
             int gp = p0 + pp;
-            As[pp][ii] = (gp < ke) ? loadA(g, i0 + ii, gp) : zmake(0, 0);
+            As[pp][ii] = (gp < ke) ? loadA(g, i0 + ii, gp) : cmk<C>(0, 0);
             int jj = e & 63;
-            Bs[pp][jj] = (gp < ke) ? loadB(g, gp, j0 + jj) : zmake(0, 0);
+            Bs[pp][jj] = (gp < ke) ? loadB(g, gp, j0 + jj) : cmk<C>(0, 0);
         }
         __syncthreads();
 #pragma unroll
         for (int pp = 0; pp < GB_K; ++pp) {
-            zc a[4], b[4];
+            C a[4], b[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 a[q] = As[pp][tx + 16 * q];
@@ -93,8 +97,8 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs g)
             if (g.work) {
                 g.work[(size_t)blockIdx.z * g.m * g.n + (size_t)j * g.m + i] = acc[x][y];
             } else {
-                zc v = zmul(g.alpha, acc[x][y]);
-                zc *c = g.C + (size_t)j * g.ldc + i;
+                C v = zmul(g.alpha, acc[x][y]);
+                C *c = g.Cm + (size_t)j * g.ldc + i;
                 if (g.beta.x != 0.0 || g.beta.y != 0.0) v = zfma(g.beta, *c, v);
                 *c = v;
             }
@@ -102,41 +106,44 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs g)
     }
 }
 
-__global__ void k_splitk_reduce(GemmArgs g, int splits)
+template <class C>
+__global__ void k_splitk_reduce(GemmArgs<C> g, int splits)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t mn = (size_t)g.m * g.n;
     if (idx >= mn) return;
-    zc s = zmake(0, 0);
+    C s = cmk<C>(0, 0);
     for (int z = 0; z < splits; ++z) s = zadd(s, g.work[(size_t)z * mn + idx]);
     int i = (int)(idx % g.m), j = (int)(idx / g.m);
-    zc v = zmul(g.alpha, s);
-    zc *c = g.C + (size_t)j * g.ldc + i;
+    C v = zmul(g.alpha, s);
+    C *c = g.Cm + (size_t)j * g.ldc + i;
     if (g.beta.x != 0.0 || g.beta.y != 0.0) v = zfma(g.beta, *c, v);
     *c = v;
 }
 
-__global__ void k_scale(zc *C, int m, int n, int ldc, zc beta)
+template <class C>
+__global__ void k_scale(C *Cm, int m, int n, int ldc, C beta)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)m * n) return;
     int i = (int)(idx % m), j = (int)(idx / m);
-    zc *c = C + (size_t)j * ldc + i;
-    *c = (beta.x == 0.0 && beta.y == 0.0) ? zmake(0, 0) : zmul(beta, *c);
+    C *c = Cm + (size_t)j * ldc + i;
+    *c = (beta.x == 0 && beta.y == 0) ? cmk<C>(0, 0) : zmul(beta, *c);
 }
 
-void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, const zc *A, int lda, const zc *B,
-           int ldb, zc beta, zc *C, int ldc)
+template <class C>
+void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, C alpha, const C *A, int lda, const C *B, int ldb,
+           C beta, C *Cm, int ldc)
 {
     if (m <= 0 || n <= 0) return;
     if (k <= 0) {
         size_t mn = (size_t)m * n;
-        k_scale<<<(unsigned)((mn + 255) / 256), 256, 0, h->stream>>>(C, m, n, ldc, beta);
+        k_scale<C><<<(unsigned)((mn + 255) / 256), 256, 0, h->stream>>>(Cm, m, n, ldc, beta);
         HM_CHECK_LAUNCH();
         count_launch(h);
         return;
     }
-    GemmArgs g;
+    GemmArgs<C> g;
     g.opA = (opA == 'C');
     g.opB = (opB == 'C');
     g.m = m;
@@ -148,7 +155,7 @@ void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, co
     g.lda = lda;
     g.B = B;
     g.ldb = ldb;
-    g.C = C;
+    g.Cm = Cm;
     g.ldc = ldc;
     int gm = (m + GB_M - 1) / GB_M, gn = (n + GB_N - 1) / GB_N;
     int tiles = gm * gn;
@@ -159,18 +166,18 @@ void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, co
     if (splits > 1) {
         g.kchunk = ((k + splits - 1) / splits + GB_K - 1) / GB_K * GB_K;
         splits = (k + g.kchunk - 1) / g.kchunk;
-        g.work = (zc *)dalloc(h, sizeof(zc) * (size_t)m * n * splits);
-        k_zgemm<<<dim3(gm, gn, splits), 256, 0, h->stream>>>(g);
+        g.work = (C *)dalloc(h, sizeof(C) * (size_t)m * n * splits);
+        k_zgemm<C><<<dim3(gm, gn, splits), 256, 0, h->stream>>>(g);
         HM_CHECK_LAUNCH();
         size_t mn = (size_t)m * n;
-        k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, h->stream>>>(g, splits);
+        k_splitk_reduce<C><<<(unsigned)((mn + 255) / 256), 256, 0, h->stream>>>(g, splits);
         HM_CHECK_LAUNCH();
         count_launch(h, 2);
         dfree(h, g.work);
     } else {
         g.work = nullptr;
         g.kchunk = k;
-        k_zgemm<<<dim3(gm, gn, 1), 256, 0, h->stream>>>(g);
+        k_zgemm<C><<<dim3(gm, gn, 1), 256, 0, h->stream>>>(g);
         HM_CHECK_LAUNCH();
         count_launch(h);
     }
@@ -181,27 +188,29 @@ void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, zc alpha, co
 // Pivot: largest modulus in the column, ties to the lowest row.  piv[k] = row
 // swapped with k (0-based, applied in order k = 0..n-1).  info: 0 or k+1 on a zero pivot.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_getrf(int n, zc *A, int lda, int *piv, int *info)
+template <class C>
+__global__ void __launch_bounds__(1024) k_getrf(int n, C *A, int lda, int *piv, int *info)
 {
-    __shared__ double sv[33];
+    typedef typename CReal<C>::R R;
+    __shared__ R sv[33];
     __shared__ int si[33];
     __shared__ int s_p;
-    __shared__ zc s_inv;
+    __shared__ C s_inv;
     const int tid = threadIdx.x, nt = blockDim.x;
     int bad = 0;
     for (int k = 0; k < n; ++k) {
         // argmax |A[i,k]|, i >= k
-        double bv = -1.0;
+        R bv = -1;
         int bi = 0x7fffffff;
         for (int i = k + tid; i < n; i += nt) {
-            double v = zabs2(A[(size_t)k * lda + i]);
+            R v = zabs2(A[(size_t)k * lda + i]);
             if (v > bv || (v == bv && i < bi)) {
                 bv = v;
                 bi = i;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            double v2 = __shfl_down_sync(0xffffffff, bv, o);
+            R v2 = __shfl_down_sync(0xffffffff, bv, o);
             int i2 = __shfl_down_sync(0xffffffff, bi, o);
             if (v2 > bv || (v2 == bv && i2 < bi)) {
                 bv = v2;
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(1024) k_getrf(int n, zc *A, int lda, int *piv,
         }
         __syncthreads();
         if (tid == 0) {
-            double v = sv[0];
+            R v = sv[0];
             int ii = si[0];
             for (int w = 1; w < (nt + 31) / 32; ++w)
                 if (sv[w] > v || (sv[w] == v && si[w] < ii)) {
@@ -223,25 +232,25 @@ __global__ void __launch_bounds__(1024) k_getrf(int n, zc *A, int lda, int *piv,
                 }
             s_p = ii;
             piv[k] = ii;
-            if (!(v > 0.0)) {
+            if (!(v > 0)) {
                 if (!bad) *info = k + 1;
                 bad = 1;
-                s_inv = zmake(0, 0);
+                s_inv = cmk<C>(0, 0);
             } else {
-                zc pv = A[(size_t)k * lda + ii];
-                s_inv = zdiv(zmake(1, 0), pv);
+                C pv = A[(size_t)k * lda + ii];
+                s_inv = zdiv(cmk<C>(1, 0), pv);
             }
         }
         __syncthreads();
         const int p = s_p;
         if (p != k)
             for (int j = tid; j < n; j += nt) {
-                zc t = A[(size_t)j * lda + k];
+                C t = A[(size_t)j * lda + k];
                 A[(size_t)j * lda + k] = A[(size_t)j * lda + p];
                 A[(size_t)j * lda + p] = t;
             }
         __syncthreads();
-        const zc inv = s_inv;
+        const C inv = s_inv;
         for (int i = k + 1 + tid; i < n; i += nt) A[(size_t)k * lda + i] = zmul(A[(size_t)k * lda + i], inv);
         __syncthreads();
         const int m = n - k - 1;
@@ -256,11 +265,12 @@ __global__ void __launch_bounds__(1024) k_getrf(int n, zc *A, int lda, int *piv,
     }
 }
 
-void zgetrf(hm_handle_s *h, int n, zc *A, int lda, int *piv, int *d_info)
+template <class C>
+void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
 {
     if (n <= 0) return;
     int T = n >= 512 ? 1024 : (n >= 128 ? 512 : 256);
-    k_getrf<<<1, T, 0, h->stream>>>(n, A, lda, piv, d_info);
+    k_getrf<C><<<1, T, 0, h->stream>>>(n, A, lda, piv, d_info);
     HM_CHECK_LAUNCH();
     count_launch(h);
     h->flops_factor += 8.0 / 3.0 * n * (double)n * n;
@@ -269,25 +279,27 @@ void zgetrf(hm_handle_s *h, int n, zc *A, int lda, int *piv, int *d_info)
 // ---------------------------------------------------------------------------
 // Row interchanges and triangular solves on multi-vectors X (rows x cols, ld)
 // ---------------------------------------------------------------------------
-__global__ void k_laswp(zc *X, int ld, int cols, const int *piv, int n)
+template <class C>
+__global__ void k_laswp(C *X, int ld, int cols, const int *piv, int n)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cols) return;
-    zc *x = X + (size_t)j * ld;
+    C *x = X + (size_t)j * ld;
     for (int k = 0; k < n; ++k) {
         int p = piv[k];
         if (p != k) {
-            zc t = x[k];
+            C t = x[k];
             x[k] = x[p];
             x[p] = t;
         }
     }
 }
 
-void zlaswp(hm_handle_s *h, MV X, const int *piv, int n)
+template <class C>
+void zlaswp(hm_handle_s *h, MVT<C> X, const int *piv, int n)
 {
     if (X.cols <= 0 || n <= 0) return;
-    k_laswp<<<(X.cols + 127) / 128, 128, 0, h->stream>>>(X.p, X.ld, X.cols, piv, n);
+    k_laswp<C><<<(X.cols + 127) / 128, 128, 0, h->stream>>>(X.p, X.ld, X.cols, piv, n);
     HM_CHECK_LAUNCH();
     count_launch(h);
 }
@@ -297,10 +309,12 @@ void zlaswp(hm_handle_s *h, MV X, const int *piv, int n)
 #define TRS_T 256
 
 // mode 0: X = L^-1 X (unit lower); 1: X = U^-1 X (upper); 2: X = U^-H X (U^H lower, non-unit)
-__global__ void __launch_bounds__(TRS_T) k_trsm_left(int mode, const zc *__restrict__ T, int ldt, int n, zc *X, int ldx,
+template <class C>
+__global__ void __launch_bounds__(TRS_T) k_trsm_left(int mode, const C *__restrict__ T, int ldt, int n, C *X, int ldx,
                                                       int cols)
 {
-    extern __shared__ zc xs[];  // [TRS_CB][n]
+    extern __shared__ __align__(16) unsigned char trs_raw[];
+    C *xs = (C *)trs_raw;  // [TRS_CB][n]
     const int c0 = blockIdx.x * TRS_CB;
     const int nc = min(TRS_CB, cols - c0);
     const int tid = threadIdx.x;
@@ -345,43 +359,60 @@ __global__ void __launch_bounds__(TRS_T) k_trsm_left(int mode, const zc *__restr
     }
 }
 
-static void trsm_left(hm_handle_s *h, int mode, const zc *T, int ldt, int n, MV X)
+template <class C>
+static void trsm_left(hm_handle_s *h, int mode, const C *T, int ldt, int n, MVT<C> X)
 {
     if (X.cols <= 0 || n <= 0) return;
-    size_t smem = sizeof(zc) * TRS_CB * n;
-    if (smem > 48 * 1024) HM_CUDA(cudaFuncSetAttribute(k_trsm_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_trsm_left<<<(X.cols + TRS_CB - 1) / TRS_CB, TRS_T, smem, h->stream>>>(mode, T, ldt, n, X.p, X.ld, X.cols);
+    size_t smem = sizeof(C) * TRS_CB * n;
+    if (smem > 48 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(k_trsm_left<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_trsm_left<C><<<(X.cols + TRS_CB - 1) / TRS_CB, TRS_T, smem, h->stream>>>(mode, T, ldt, n, X.p, X.ld, X.cols);
     HM_CHECK_LAUNCH();
     count_launch(h);
     h->flops_factor += 4.0 * n * (double)n * X.cols;
 }
 
-void ztrsm_lln(hm_handle_s *h, const zc *L, int ldl, int n, MV X) { trsm_left(h, 0, L, ldl, n, X); }
-void ztrsm_lun(hm_handle_s *h, const zc *U, int ldu, int n, MV X) { trsm_left(h, 1, U, ldu, n, X); }
-void ztrsm_luh(hm_handle_s *h, const zc *U, int ldu, int n, MV X) { trsm_left(h, 2, U, ldu, n, X); }
+template <class C>
+void ztrsm_lln(hm_handle_s *h, const C *L, int ldl, int n, MVT<C> X)
+{
+    trsm_left(h, 0, L, ldl, n, X);
+}
+template <class C>
+void ztrsm_lun(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X)
+{
+    trsm_left(h, 1, U, ldu, n, X);
+}
+template <class C>
+void ztrsm_luh(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X)
+{
+    trsm_left(h, 2, U, ldu, n, X);
+}
 
 // X = X U^-1 (X rows x n): one thread per row, sequential over columns.
-__global__ void k_trsm_right_upper(const zc *__restrict__ U, int ldu, int n, zc *X, int ldx, int rows)
+template <class C>
+__global__ void k_trsm_right_upper(const C *__restrict__ U, int ldu, int n, C *X, int ldx, int rows)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     for (int j = 0; j < n; ++j) {
-        zc s = X[(size_t)j * ldx + r];
+        C s = X[(size_t)j * ldx + r];
         for (int i = 0; i < j; ++i) s = zsub(s, zmul(X[(size_t)i * ldx + r], U[(size_t)j * ldu + i]));
         X[(size_t)j * ldx + r] = zdiv(s, U[(size_t)j * ldu + j]);
     }
 }
 
-void ztrsm_run(hm_handle_s *h, const zc *U, int ldu, int n, MV X)
+template <class C>
+void ztrsm_run(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X)
 {
     if (X.rows <= 0 || n <= 0) return;
-    k_trsm_right_upper<<<(X.rows + 63) / 64, 64, 0, h->stream>>>(U, ldu, n, X.p, X.ld, X.rows);
+    k_trsm_right_upper<C><<<(X.rows + 63) / 64, 64, 0, h->stream>>>(U, ldu, n, X.p, X.ld, X.rows);
     HM_CHECK_LAUNCH();
     count_launch(h);
     h->flops_factor += 4.0 * n * (double)n * X.rows;
 }
 
-__global__ void k_copy2d(zc *dst, int ldd, const zc *src, int lds, int rows, int cols)
+template <class C>
+__global__ void k_copy2d(C *dst, int ldd, const C *src, int lds, int rows, int cols)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)rows * cols) return;
@@ -389,16 +420,18 @@ __global__ void k_copy2d(zc *dst, int ldd, const zc *src, int lds, int rows, int
     dst[(size_t)j * ldd + i] = src[(size_t)j * lds + i];
 }
 
-void zcopy2d(hm_handle_s *h, MV dst, MV src)
+template <class C>
+void zcopy2d(hm_handle_s *h, MVT<C> dst, MVT<C> src)
 {
     size_t n = (size_t)src.rows * src.cols;
     if (n == 0) return;
-    k_copy2d<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dst.p, dst.ld, src.p, src.ld, src.rows, src.cols);
+    k_copy2d<C><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dst.p, dst.ld, src.p, src.ld, src.rows, src.cols);
     HM_CHECK_LAUNCH();
     count_launch(h);
 }
 
-__global__ void k_scale_cols(zc *X, int ld, int rows, int cols, const double *s)
+template <class C>
+__global__ void k_scale_cols(C *X, int ld, int rows, int cols, const typename CReal<C>::R *s)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)rows * cols) return;
@@ -406,11 +439,12 @@ __global__ void k_scale_cols(zc *X, int ld, int rows, int cols, const double *s)
     X[(size_t)j * ld + i] = zscale(X[(size_t)j * ld + i], s[j]);
 }
 
-void zscale_cols(hm_handle_s *h, MV X, const double *d_s)
+template <class C>
+void zscale_cols(hm_handle_s *h, MVT<C> X, const typename CReal<C>::R *d_s)
 {
     size_t n = (size_t)X.rows * X.cols;
     if (n == 0) return;
-    k_scale_cols<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(X.p, X.ld, X.rows, X.cols, d_s);
+    k_scale_cols<C><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(X.p, X.ld, X.rows, X.cols, d_s);
     HM_CHECK_LAUNCH();
     count_launch(h);
 }
@@ -419,63 +453,67 @@ void zscale_cols(hm_handle_s *h, MV X, const double *d_s)
 // Householder QR, one CTA per matrix: A (m x K, ld m) -> Q (m x r), R (r x K), r = min(m, K).
 // H_j = I - 2 v v^H / (v^H v), v = x - alpha e_1, alpha = -exp(i arg x_0) |x|, H_j x = alpha e_1.
 // ---------------------------------------------------------------------------
+template <class C>
 struct QRDesc {
-    zc *A;       // input, overwritten (reflectors)
+    C *A;        // input, overwritten (reflectors)
     int m, K;
-    zc *Q;       // m x r
-    zc *R;       // r x K
-    double *beta;  // workspace [r]
+    C *Q;        // m x r
+    C *R;        // r x K
+    typename CReal<C>::R *beta;  // workspace [r]
 };
 
 #define QR_T 512
 
-__device__ double qr_block_sum(double v, double *sh)
+template <class R>
+__device__ R qr_block_sum(R v, R *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffff, v, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0;
+        R s = 0;
         for (int w = 0; w < QR_T / 32; ++w) s += sh[w];
         sh[32] = s;
     }
     __syncthreads();
-    double r = sh[32];
+    R r = sh[32];
     __syncthreads();
     return r;
 }
 
-__global__ void __launch_bounds__(QR_T) k_qr(const QRDesc *__restrict__ descs)
+template <class C>
+__global__ void __launch_bounds__(QR_T) k_qr(const QRDesc<C> *__restrict__ descs)
 {
-    const QRDesc d = descs[blockIdx.x];
+    typedef typename CReal<C>::R R;
+    const QRDesc<C> d = descs[blockIdx.x];
     const int m = d.m, K = d.K, r = min(m, K);
-    __shared__ double sh[33];
-    __shared__ zc s_alpha;
+    __shared__ R sh[33];
+    __shared__ C s_alpha;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_T / 32;
-    zc *A = d.A;
+    C *A = d.A;
     for (int j = 0; j < r; ++j) {
-        zc *x = A + (size_t)j * m;
-        double nrm2 = 0.0;
+        C *x = A + (size_t)j * m;
+        R nrm2 = 0;
         for (int i = j + tid; i < m; i += QR_T) nrm2 += zabs2(x[i]);
         nrm2 = qr_block_sum(nrm2, sh);
-        double nrm = sqrt(nrm2);
+        R nrm = sqrt(nrm2);
         if (tid == 0) {
-            zc x0 = x[j];
-            double a0 = sqrt(zabs2(x0));
-            zc ph = a0 > 0 ? zscale(x0, 1.0 / a0) : zmake(1, 0);
-            zc alpha = zscale(ph, -nrm);
+            C x0 = x[j];
+            R a0 = sqrt(zabs2(x0));
+            C ph = a0 > 0 ? zscale(x0, (R)1 / a0) : cmk<C>(1, 0);
+            C alpha = zscale(ph, -nrm);
             s_alpha = alpha;
             // v = x - alpha e1; v^H v = 2 (|x|^2 + |x| |x0|)
             x[j] = zsub(x0, alpha);
-            double vhv = 2.0 * (nrm2 + nrm * a0);
-            d.beta[j] = vhv > 0 ? 2.0 / vhv : 0.0;
+            R vhv = 2 * (nrm2 + nrm * a0);
+            d.beta[j] = vhv > 0 ? 2 / vhv : 0;
         }
         __syncthreads();
-        const double beta = d.beta[j];
+        const R beta = d.beta[j];
         // apply H to columns c > j: a -= beta v (v^H a)
         for (int c = j + 1 + warp; c < K; c += nw) {
-            zc *a = A + (size_t)c * m;
-            zc s = zmake(0, 0);
+            C *a = A + (size_t)c * m;
+            C s = cmk<C>(0, 0);
             for (int i = j + lane; i < m; i += 32) s = zfmac(x[i], a[i], s);
             for (int o = 16; o > 0; o >>= 1) {
                 s.x += __shfl_xor_sync(0xffffffff, s.x, o);
@@ -488,21 +526,21 @@ __global__ void __launch_bounds__(QR_T) k_qr(const QRDesc *__restrict__ descs)
         // R row j
         if (tid == 0) d.R[(size_t)j * r + j] = s_alpha;
         for (int c = j + 1 + tid; c < K; c += QR_T) d.R[(size_t)c * r + j] = A[(size_t)c * m + j];
-        for (int c = tid; c < j && c < K; c += QR_T) d.R[(size_t)c * r + j] = zmake(0, 0);
+        for (int c = tid; c < j && c < K; c += QR_T) d.R[(size_t)c * r + j] = cmk<C>(0, 0);
         __syncthreads();
     }
     // Q = H_0 ... H_{r-1} [I_r; 0]
     for (int e = tid; e < m * r; e += QR_T) {
         int i = e % m, c = e / m;
-        d.Q[(size_t)c * m + i] = zmake(i == c ? 1.0 : 0.0, 0.0);
+        d.Q[(size_t)c * m + i] = cmk<C>(i == c ? 1 : 0, 0);
     }
     __syncthreads();
     for (int j = r - 1; j >= 0; --j) {
-        const zc *v = A + (size_t)j * m;
-        const double beta = d.beta[j];
+        const C *v = A + (size_t)j * m;
+        const R beta = d.beta[j];
         for (int c = j + warp; c < r; c += nw) {
-            zc *q = d.Q + (size_t)c * m;
-            zc s = zmake(0, 0);
+            C *q = d.Q + (size_t)c * m;
+            C s = cmk<C>(0, 0);
             for (int i = j + lane; i < m; i += 32) s = zfmac(v[i], q[i], s);
             for (int o = 16; o > 0; o >>= 1) {
                 s.x += __shfl_xor_sync(0xffffffff, s.x, o);
@@ -520,27 +558,35 @@ __global__ void __launch_bounds__(QR_T) k_qr(const QRDesc *__restrict__ descs)
 // Y (q x q) unitary; on exit M holds X Sigma (orthogonal columns), S[j] = |col j|,
 // ord[] = column order by decreasing S.  Round-robin pairs, one warp per pair.
 // ---------------------------------------------------------------------------
+template <class C>
 struct SVDDesc {
-    zc *M;
+    C *M;
     int p, q;
-    zc *Y;
-    double *S;
+    C *Y;
+    typename CReal<C>::R *S;
     int *ord;
 };
+
+// Relative size of an off-diagonal inner product below which a Jacobi rotation is skipped.
+template <class R> __device__ __forceinline__ R jacobi_eps();
+template <> __device__ __forceinline__ double jacobi_eps<double>() { return 1e-15; }
+template <> __device__ __forceinline__ float jacobi_eps<float>() { return 1e-7f; }
 
 #define SVD_T 512
 #define SVD_QMAX 4096
 
-__global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc *__restrict__ descs)
+template <class C>
+__global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc<C> *__restrict__ descs)
 {
-    const SVDDesc d = descs[blockIdx.x];
+    typedef typename CReal<C>::R R;
+    const SVDDesc<C> d = descs[blockIdx.x];
     const int p = d.p, q = d.q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = SVD_T / 32;
     __shared__ int s_rot;
     extern __shared__ int perm[];  // [q rounded up to even]
     for (int e = tid; e < q * q; e += SVD_T) {
         int i = e % q, j = e / q;
-        d.Y[(size_t)j * q + i] = zmake(i == j ? 1.0 : 0.0, 0.0);
+        d.Y[(size_t)j * q + i] = cmk<C>(i == j ? 1 : 0, 0);
     }
     const int qe = (q + 1) & ~1;  // even count (a dummy column when q is odd)
     for (int i = tid; i < qe; i += SVD_T) perm[i] = i;
@@ -557,9 +603,9 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc *__restrict__ descs
                     a = b;
                     b = t;
                 }
-                zc *ca = d.M + (size_t)a * p, *cb = d.M + (size_t)b * p;
-                double al = 0, be = 0;
-                zc ga = zmake(0, 0);
+                C *ca = d.M + (size_t)a * p, *cb = d.M + (size_t)b * p;
+                R al = 0, be = 0;
+                C ga = cmk<C>(0, 0);
                 for (int i = lane; i < p; i += 32) {
                     al += zabs2(ca[i]);
                     be += zabs2(cb[i]);
@@ -571,22 +617,22 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc *__restrict__ descs
                     ga.x += __shfl_xor_sync(0xffffffff, ga.x, o);
                     ga.y += __shfl_xor_sync(0xffffffff, ga.y, o);
                 }
-                double g = sqrt(zabs2(ga));
-                if (!(g > 1e-15 * sqrt(al * be)) || g == 0.0) continue;
+                R g = sqrt(zabs2(ga));
+                if (!(g > jacobi_eps<R>() * sqrt(al * be)) || g == 0) continue;
                 if (lane == 0) s_rot = 1;
-                zc eph = zscale(ga, 1.0 / g);  // exp(i phi)
-                double zeta = (be - al) / (2.0 * g);
-                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                zc sem = zscale(zconj(eph), s), sep = zscale(eph, s);
+                C eph = zscale(ga, (R)1 / g);  // exp(i phi)
+                R zeta = (be - al) / (2 * g);
+                R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt(1 + zeta * zeta));
+                R c = 1 / sqrt(1 + t * t), s = c * t;
+                C sem = zscale(zconj(eph), s), sep = zscale(eph, s);
                 for (int i = lane; i < p; i += 32) {
-                    zc x = ca[i], y = cb[i];
+                    C x = ca[i], y = cb[i];
                     ca[i] = zsub(zscale(x, c), zmul(sem, y));
                     cb[i] = zadd(zmul(sep, x), zscale(y, c));
                 }
-                zc *ya = d.Y + (size_t)a * q, *yb = d.Y + (size_t)b * q;
+                C *ya = d.Y + (size_t)a * q, *yb = d.Y + (size_t)b * q;
                 for (int i = lane; i < q; i += 32) {
-                    zc x = ya[i], y = yb[i];
+                    C x = ya[i], y = yb[i];
                     ya[i] = zsub(zscale(x, c), zmul(sem, y));
                     yb[i] = zadd(zmul(sep, x), zscale(y, c));
                 }
@@ -604,7 +650,7 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc *__restrict__ descs
         __syncthreads();
     }
     for (int j = warp; j < q; j += nw) {
-        double s = 0;
+        R s = 0;
         for (int i = lane; i < p; i += 32) s += zabs2(d.M[(size_t)j * p + i]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
         if (lane == 0) d.S[j] = sqrt(s);
@@ -627,16 +673,18 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc *__restrict__ descs
 
 // Assemble the truncated factors: Uo[:, t] = Q_U * (X col ord[t]) / S * sqrt(S) ... done as
 // gather + scale: G[:, t] = M[:, ord[t]] * f(S), H[:, t] = Y[:, ord[t]] * sqrt(S)
-__global__ void k_gather_cols(const zc *M, int p, const int *ord, const double *S, int kk, zc *G, int mode)
+template <class C>
+__global__ void k_gather_cols(const C *M, int p, const int *ord, const typename CReal<C>::R *S, int kk, C *G, int mode)
 {
+    typedef typename CReal<C>::R R;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)p * kk) return;
     int i = (int)(idx % p), t = (int)(idx / p);
     int c = ord[t];
-    double s = S[c];
-    double f;
+    R s = S[c];
+    R f;
     if (mode == 0)
-        f = s > 0 ? 1.0 / sqrt(s) : 0.0;  // X Sigma -> X sqrt(Sigma)
+        f = s > 0 ? 1 / sqrt(s) : 0;  // X Sigma -> X sqrt(Sigma)
     else
         f = sqrt(s);  // Y -> Y sqrt(Sigma)
     G[(size_t)t * p + i] = zscale(M[(size_t)c * p + i], f);
@@ -646,61 +694,65 @@ __global__ void k_gather_cols(const zc *M, int p, const int *ord, const double *
 // Truncated recompression of U V^H (batched): QR of both factors, SVD of the core
 // R_U R_V^H, keep the smallest rank k' with sqrt(sum_{i>k'} s_i^2) <= tol |s|_2.
 // ---------------------------------------------------------------------------
+template <class C>
 struct TruncJob {
+    typedef typename CReal<C>::R R;
     int m, n, K;
-    const zc *U;
+    const C *U;
     int ldu;
-    const zc *V;
+    const C *V;
     int ldv;
     int kmax;
     // work
-    zc *Ua, *Va, *QU, *QV, *RU, *RV, *Mc, *Y;
-    double *bU, *bV, *S;
+    C *Ua, *Va, *QU, *QV, *RU, *RV, *Mc, *Y;
+    R *bU, *bV, *S;
     int *ord;
     int r1, r2;
 };
 
-static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob> &jobs)
+template <class C>
+static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
 {
+    typedef typename CReal<C>::R R;
     // workspace and copies
-    std::vector<QRDesc> qd;
+    std::vector<QRDesc<C>> qd;
     for (auto &J : jobs) {
         J.r1 = std::min(J.m, J.K);
         J.r2 = std::min(J.n, J.K);
-        J.Ua = (zc *)dalloc(h, sizeof(zc) * (size_t)J.m * J.K);
-        J.Va = (zc *)dalloc(h, sizeof(zc) * (size_t)J.n * J.K);
-        J.QU = (zc *)dalloc(h, sizeof(zc) * (size_t)J.m * J.r1);
-        J.QV = (zc *)dalloc(h, sizeof(zc) * (size_t)J.n * J.r2);
-        J.RU = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r1 * J.K);
-        J.RV = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r2 * J.K);
-        J.Mc = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r1 * J.r2);
-        J.Y = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r2 * J.r2);
-        J.bU = (double *)dalloc(h, sizeof(double) * (J.r1 + J.r2 + J.r2));
+        J.Ua = (C *)dalloc(h, sizeof(C) * (size_t)J.m * J.K);
+        J.Va = (C *)dalloc(h, sizeof(C) * (size_t)J.n * J.K);
+        J.QU = (C *)dalloc(h, sizeof(C) * (size_t)J.m * J.r1);
+        J.QV = (C *)dalloc(h, sizeof(C) * (size_t)J.n * J.r2);
+        J.RU = (C *)dalloc(h, sizeof(C) * (size_t)J.r1 * J.K);
+        J.RV = (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * J.K);
+        J.Mc = (C *)dalloc(h, sizeof(C) * (size_t)J.r1 * J.r2);
+        J.Y = (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * J.r2);
+        J.bU = (R *)dalloc(h, sizeof(R) * (J.r1 + J.r2 + J.r2));
         J.bV = J.bU + J.r1;
         J.S = J.bV + J.r2;
         J.ord = (int *)dalloc(h, sizeof(int) * J.r2);
-        zcopy2d(h, MV{J.Ua, J.m, J.K, J.m}, MV{(zc *)J.U, J.m, J.K, J.ldu});
-        zcopy2d(h, MV{J.Va, J.n, J.K, J.n}, MV{(zc *)J.V, J.n, J.K, J.ldv});
-        qd.push_back(QRDesc{J.Ua, J.m, J.K, J.QU, J.RU, J.bU});
-        qd.push_back(QRDesc{J.Va, J.n, J.K, J.QV, J.RV, J.bV});
+        zcopy2d(h, MVT<C>{J.Ua, J.m, J.K, J.m}, MVT<C>{(C *)J.U, J.m, J.K, J.ldu});
+        zcopy2d(h, MVT<C>{J.Va, J.n, J.K, J.n}, MVT<C>{(C *)J.V, J.n, J.K, J.ldv});
+        qd.push_back(QRDesc<C>{J.Ua, J.m, J.K, J.QU, J.RU, J.bU});
+        qd.push_back(QRDesc<C>{J.Va, J.n, J.K, J.QV, J.RV, J.bV});
         h->flops_factor += 16.0 * ((double)J.m + J.n) * J.K * J.K;
     }
-    QRDesc *d_qd = (QRDesc *)dalloc(h, sizeof(QRDesc) * qd.size());
-    HM_CUDA(cudaMemcpyAsync(d_qd, qd.data(), sizeof(QRDesc) * qd.size(), cudaMemcpyHostToDevice, h->stream));
-    k_qr<<<(unsigned)qd.size(), QR_T, 0, h->stream>>>(d_qd);
+    QRDesc<C> *d_qd = (QRDesc<C> *)dalloc(h, sizeof(QRDesc<C>) * qd.size());
+    HM_CUDA(cudaMemcpyAsync(d_qd, qd.data(), sizeof(QRDesc<C>) * qd.size(), cudaMemcpyHostToDevice, h->stream));
+    k_qr<C><<<(unsigned)qd.size(), QR_T, 0, h->stream>>>(d_qd);
     HM_CHECK_LAUNCH();
     count_launch(h);
     // core M = R_U R_V^H
     for (auto &J : jobs)
-        zgemm(h, 'N', 'C', J.r1, J.r2, J.K, zmake(1, 0), J.RU, J.r1, J.RV, J.r2, zmake(0, 0), J.Mc, J.r1);
-    std::vector<SVDDesc> sd;
-    for (auto &J : jobs) sd.push_back(SVDDesc{J.Mc, J.r1, J.r2, J.Y, J.S, J.ord});
+        zgemm<C>(h, 'N', 'C', J.r1, J.r2, J.K, cmk<C>(1, 0), J.RU, J.r1, J.RV, J.r2, cmk<C>(0, 0), J.Mc, J.r1);
+    std::vector<SVDDesc<C>> sd;
+    for (auto &J : jobs) sd.push_back(SVDDesc<C>{J.Mc, J.r1, J.r2, J.Y, J.S, J.ord});
     int qmax = 0;
     for (auto &J : jobs) qmax = std::max(qmax, J.r2);
     if (qmax > SVD_QMAX) throw HmError{HM_ERR_NUMERIC, "recompression core too large: " + std::to_string(qmax)};
-    SVDDesc *d_sd = (SVDDesc *)dalloc(h, sizeof(SVDDesc) * sd.size());
-    HM_CUDA(cudaMemcpyAsync(d_sd, sd.data(), sizeof(SVDDesc) * sd.size(), cudaMemcpyHostToDevice, h->stream));
-    k_svd<<<(unsigned)sd.size(), SVD_T, sizeof(int) * (qmax + 2), h->stream>>>(d_sd);
+    SVDDesc<C> *d_sd = (SVDDesc<C> *)dalloc(h, sizeof(SVDDesc<C>) * sd.size());
+    HM_CUDA(cudaMemcpyAsync(d_sd, sd.data(), sizeof(SVDDesc<C>) * sd.size(), cudaMemcpyHostToDevice, h->stream));
+    k_svd<C><<<(unsigned)sd.size(), SVD_T, sizeof(int) * (qmax + 2), h->stream>>>(d_sd);
     HM_CHECK_LAUNCH();
     count_launch(h);
     HM_CUDA(cudaStreamSynchronize(h->stream));
@@ -709,8 +761,9 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob> &jobs)
 }
 
 // returns the kept rank; allocates *Uo (m x k'), *Vo (n x k')
-static int trunc_stage2(hm_handle_s *h, TruncJob &J, const std::vector<double> &S, const std::vector<int> &ord,
-                        double tol, zc **Uo, zc **Vo)
+template <class C>
+static int trunc_stage2(hm_handle_s *h, TruncJob<C> &J, const std::vector<double> &S, const std::vector<int> &ord,
+                        double tol, C **Uo, C **Vo)
 {
     double tot = 0;
     for (double s : S) tot += s * s;
@@ -724,21 +777,21 @@ static int trunc_stage2(hm_handle_s *h, TruncJob &J, const std::vector<double> &
     }
     if (tot == 0.0) kk = 0;
     kk = std::min(kk, J.kmax > 0 ? J.kmax : kk);
-    zc *G = nullptr, *Hh = nullptr;
+    C *G = nullptr, *Hh = nullptr;
     *Uo = nullptr;
     *Vo = nullptr;
     if (kk > 0) {
-        G = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r1 * kk);
-        Hh = (zc *)dalloc(h, sizeof(zc) * (size_t)J.r2 * kk);
+        G = (C *)dalloc(h, sizeof(C) * (size_t)J.r1 * kk);
+        Hh = (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * kk);
         size_t n1 = (size_t)J.r1 * kk, n2 = (size_t)J.r2 * kk;
-        k_gather_cols<<<(unsigned)((n1 + 255) / 256), 256, 0, h->stream>>>(J.Mc, J.r1, J.ord, J.S, kk, G, 0);
-        k_gather_cols<<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(J.Y, J.r2, J.ord, J.S, kk, Hh, 1);
+        k_gather_cols<C><<<(unsigned)((n1 + 255) / 256), 256, 0, h->stream>>>(J.Mc, J.r1, J.ord, J.S, kk, G, 0);
+        k_gather_cols<C><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(J.Y, J.r2, J.ord, J.S, kk, Hh, 1);
         HM_CHECK_LAUNCH();
         count_launch(h, 2);
-        *Uo = (zc *)dalloc(h, sizeof(zc) * (size_t)J.m * kk);
-        *Vo = (zc *)dalloc(h, sizeof(zc) * (size_t)J.n * kk);
-        zgemm(h, 'N', 'N', J.m, kk, J.r1, zmake(1, 0), J.QU, J.m, G, J.r1, zmake(0, 0), *Uo, J.m);
-        zgemm(h, 'N', 'N', J.n, kk, J.r2, zmake(1, 0), J.QV, J.n, Hh, J.r2, zmake(0, 0), *Vo, J.n);
+        *Uo = (C *)dalloc(h, sizeof(C) * (size_t)J.m * kk);
+        *Vo = (C *)dalloc(h, sizeof(C) * (size_t)J.n * kk);
+        zgemm<C>(h, 'N', 'N', J.m, kk, J.r1, cmk<C>(1, 0), J.QU, J.m, G, J.r1, cmk<C>(0, 0), *Uo, J.m);
+        zgemm<C>(h, 'N', 'N', J.n, kk, J.r2, cmk<C>(1, 0), J.QV, J.n, Hh, J.r2, cmk<C>(0, 0), *Vo, J.n);
         dfree(h, G);
         dfree(h, Hh);
     }
@@ -755,27 +808,32 @@ static int trunc_stage2(hm_handle_s *h, TruncJob &J, const std::vector<double> &
     return kk;
 }
 
-static void fetch_sv(hm_handle_s *h, std::vector<TruncJob> &jobs, std::vector<std::vector<double>> &S,
+template <class C>
+static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector<std::vector<double>> &S,
                      std::vector<std::vector<int>> &ord)
 {
+    typedef typename CReal<C>::R R;
     S.resize(jobs.size());
     ord.resize(jobs.size());
+    std::vector<std::vector<R>> Sr(jobs.size());
     for (size_t i = 0; i < jobs.size(); ++i) {
-        S[i].resize(jobs[i].r2);
+        Sr[i].resize(jobs[i].r2);
         ord[i].resize(jobs[i].r2);
-        HM_CUDA(cudaMemcpyAsync(S[i].data(), jobs[i].S, sizeof(double) * jobs[i].r2, cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaMemcpyAsync(Sr[i].data(), jobs[i].S, sizeof(R) * jobs[i].r2, cudaMemcpyDeviceToHost, h->stream));
         HM_CUDA(cudaMemcpyAsync(ord[i].data(), jobs[i].ord, sizeof(int) * jobs[i].r2, cudaMemcpyDeviceToHost, h->stream));
     }
     HM_CUDA(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < jobs.size(); ++i) S[i].assign(Sr[i].begin(), Sr[i].end());
 }
 
-int truncate_lr(hm_handle_s *h, int m, int n, int K, const zc *U, int ldu, const zc *V, int ldv, double tol, int kmax,
-                zc **Uo, zc **Vo)
+template <class C>
+int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const C *V, int ldv, double tol, int kmax,
+                C **Uo, C **Vo)
 {
     *Uo = *Vo = nullptr;
     if (K <= 0 || m <= 0 || n <= 0) return 0;
-    std::vector<TruncJob> jobs(1);
-    jobs[0] = TruncJob{};
+    std::vector<TruncJob<C>> jobs(1);
+    jobs[0] = TruncJob<C>{};
     jobs[0].m = m;
     jobs[0].n = n;
     jobs[0].K = K;
@@ -793,17 +851,18 @@ int truncate_lr(hm_handle_s *h, int m, int n, int K, const zc *U, int ldu, const
 
 // Recompress the low-rank leaves blks (U, V with ranks[i] columns) in one batch;
 // replaces b->U, b->V, b->k.
-void batched_truncate(hm_handle_s *h, std::vector<Block *> &blks, const std::vector<int> &ranks, double tol)
+template <class C>
+void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std::vector<int> &ranks, double tol)
 {
     const size_t CH = 512;  // jobs per batch (bounds the workspace)
     for (size_t s = 0; s < blks.size(); s += CH) {
         size_t e = std::min(blks.size(), s + CH);
-        std::vector<TruncJob> jobs;
+        std::vector<TruncJob<C>> jobs;
         std::vector<size_t> idx;
         for (size_t i = s; i < e; ++i) {
-            Block *b = blks[i];
+            BlockT<C> *b = blks[i];
             if (ranks[i] <= 0) continue;
-            TruncJob J{};
+            TruncJob<C> J{};
             J.m = b->nr;
             J.n = b->nc;
             J.K = ranks[i];
@@ -821,8 +880,8 @@ void batched_truncate(hm_handle_s *h, std::vector<Block *> &blks, const std::vec
         std::vector<std::vector<int>> ord;
         fetch_sv(h, jobs, S, ord);
         for (size_t t = 0; t < jobs.size(); ++t) {
-            Block *b = blks[idx[t]];
-            zc *Uo, *Vo;
+            BlockT<C> *b = blks[idx[t]];
+            C *Uo, *Vo;
             int kk = trunc_stage2(h, jobs[t], S[t], ord[t], tol, &Uo, &Vo);
             dfree(h, b->U);
             dfree(h, b->V);
@@ -832,3 +891,22 @@ void batched_truncate(hm_handle_s *h, std::vector<Block *> &blks, const std::vec
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Explicit instantiations: complex128 (the FP64 method) and complex64 (the FP32
+// factor used as a preconditioner).
+// ---------------------------------------------------------------------------
+#define HM_INST_LINALG(C)                                                                                         \
+    template void zgemm<C>(hm_handle_s *, char, char, int, int, int, C, const C *, int, const C *, int, C, C *, int); \
+    template void zgetrf<C>(hm_handle_s *, int, C *, int, int *, int *);                                          \
+    template void zlaswp<C>(hm_handle_s *, MVT<C>, const int *, int);                                             \
+    template void ztrsm_lln<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
+    template void ztrsm_lun<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
+    template void ztrsm_luh<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
+    template void ztrsm_run<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
+    template void zcopy2d<C>(hm_handle_s *, MVT<C>, MVT<C>);                                                      \
+    template void zscale_cols<C>(hm_handle_s *, MVT<C>, const typename CReal<C>::R *);                            \
+    template int truncate_lr<C>(hm_handle_s *, int, int, int, const C *, int, const C *, int, double, int, C **, C **); \
+    template void batched_truncate<C>(hm_handle_s *, std::vector<BlockT<C> *> &, const std::vector<int> &, double);
+HM_INST_LINALG(zc)
+HM_INST_LINALG(cf)

@@ -18,7 +18,8 @@ STATUS = {0: "HM_OK", 1: "HM_ERR_ARG", 2: "HM_ERR_STATE", 3: "HM_ERR_CUDA", 4: "
 Q = dict(N=0, NNODE=1, NPATCH=2, NEAR_PAIRS=3, DENSE_BLOCKS=4, LR_BLOCKS=5, CR=6, MAX_RANK=7,
          T_GEOMETRY=8, T_NEAR=9, T_DENSE=10, T_ACA=11, T_FACTOR=12, T_SOLVE=13, FLOPS_FACTOR=14,
          STORAGE=15, ACA_NONCONV=16, LAUNCHES=17, NEAR_QPOINTS=18, MEAN_RANK=19, STORAGE_FACTOR=20,
-         T_RECOMPRESS=21)
+         T_RECOMPRESS=21, REFINE_ITERS=22, REFINE_RES=23, STORAGE32=24)
+HM_FP64, HM_FP32_REFINED = 0, 1
 
 EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor", "hm_solve",
            "hm_solve_host", "hm_farfield", "hm_matvec", "hm_query", "hm_last_error", "hm_destroy",
@@ -29,7 +30,8 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
 class hm_params(ctypes.Structure):
     _fields_ = [("k0", ctypes.c_double), ("formulation", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("eta", ctypes.c_double), ("aca_tol", ctypes.c_double), ("near_delta", ctypes.c_double),
-                ("aca_max_rank", ctypes.c_int), ("precision", ctypes.c_int), ("keep_matrix", ctypes.c_int)]
+                ("aca_max_rank", ctypes.c_int), ("precision", ctypes.c_int), ("keep_matrix", ctypes.c_int),
+                ("factor_tol", ctypes.c_double), ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int)]
 
 
 class hm_body(ctypes.Structure):
@@ -130,11 +132,12 @@ class Solver:
             pass
 
     def hm_build_geometry(self, bodies, ms, nc, k0, leaf, eta, aca_tol, near_delta=0.5, aca_max_rank=0,
-                          keep_matrix=False):
+                          keep_matrix=False, precision=HM_FP64, factor_tol=0.0, refine_tol=0.0, refine_max_iter=0):
         self._bodies = make_bodies(bodies, ms)
         p = hm_params(k0=float(k0), formulation=0, leaf=int(leaf), eta=float(eta), aca_tol=float(aca_tol),
-                      near_delta=float(near_delta), aca_max_rank=int(aca_max_rank), precision=0,
-                      keep_matrix=int(bool(keep_matrix)))
+                      near_delta=float(near_delta), aca_max_rank=int(aca_max_rank), precision=int(precision),
+                      keep_matrix=int(bool(keep_matrix)), factor_tol=float(factor_tol),
+                      refine_tol=float(refine_tol), refine_max_iter=int(refine_max_iter))
         self._check(self.L.hm_build_geometry(self.h, self._bodies, len(ms), int(nc), ctypes.byref(p)))
         self.N = int(self.hm_query("N"))
         self.nnode = self.N // 2

@@ -215,3 +215,53 @@ def test_full_size_sampled_residual():
     for r in range(x.shape[0]):
         res = R @ x[r] - b[r][rows]
         assert np.linalg.norm(res) / np.linalg.norm(b[r][rows]) <= 1e-5
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_fp32_factor_with_fp64_refinement_against_dense_oracle(name):
+    # FP32 H-LU as a preconditioner, FP64 refinement against the FP64 H-matrix
+    wl, o, A, b, xo = oracle_for(name)
+    s = make_solver(wl, precision=hm.HM_FP32_REFINED)
+    s.hm_fill()
+    s.hm_factor()
+    x = s.hm_solve(wl["kdirs"], wl["pols"]).cpu().numpy()
+    assert s.hm_query("REFINE_RES") <= 1e-10
+    assert 1 <= s.hm_query("REFINE_ITERS") <= 30
+    assert s.hm_query("STORAGE32") > 0
+    for r in range(x.shape[0]):
+        err = np.linalg.norm(x[r] - xo[r]) / np.linalg.norm(xo[r])
+        res = np.linalg.norm(A @ x[r] - b[r]) / np.linalg.norm(b[r])
+        assert err <= 1e-5, (r, err)
+        assert res <= 1e-5, (r, res)
+    # the FP64 H-matrix is still available for products after the FP32 factor
+    y = s.hm_matvec(torch.tensor(x, device="cuda")).cpu().numpy()
+    assert np.linalg.norm(y - x @ A.T) / np.linalg.norm(x @ A.T) < 1e-6
+
+
+def test_fp32_refinement_reports_non_convergence():
+    # a step limit of one cannot reach a 1e-14 residual: the call reports it
+    wl, o, A, b, xo = oracle_for("sphere_d1_m1_nc8")
+    s = make_solver(wl, precision=hm.HM_FP32_REFINED, refine_tol=1e-14, refine_max_iter=1)
+    s.hm_fill()
+    s.hm_factor()
+    with pytest.raises(hm.HmError) as e:
+        s.hm_solve(wl["kdirs"], wl["pols"])
+    assert e.value.status == 6
+    assert s.hm_query("REFINE_ITERS") == 1
+
+
+def test_full_size_fp32_refined_sampled_residual():
+    wl = workloads.workload("sphere_d8_m4_nc10")
+    s = make_solver(wl, precision=hm.HM_FP32_REFINED)
+    s.hm_fill()
+    s.hm_factor()
+    x = s.hm_solve(wl["kdirs"], wl["pols"]).cpu().numpy()
+    assert s.hm_query("REFINE_RES") <= 1e-10
+    o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
+    b = o.rhs(wl["kdirs"], wl["pols"])
+    rng = np.random.default_rng(12)
+    rows = rng.choice(o.N, 48, replace=False)
+    R = o.matrix_rows(rows)
+    for r in range(x.shape[0]):
+        res = R @ x[r] - b[r][rows]
+        assert np.linalg.norm(res) / np.linalg.norm(b[r][rows]) <= 1e-5
