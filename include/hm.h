@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 typedef struct hm_handle_s *hm_handle;
+typedef struct hm_mlp_s *hm_mlp;
 
 typedef enum {
     HM_OK = 0,
@@ -113,7 +114,17 @@ enum {
     HM_Q_REFINE_ITERS = 22,/* refinement steps of the last hm_solve (HM_FP32_REFINED; 0 otherwise) */
     HM_Q_REFINE_RES = 23,  /* largest relative residual |b - A x| / |b| (FP64 H-matrix) after the last
                               hm_solve in HM_FP32_REFINED mode */
-    HM_Q_STORAGE32 = 24    /* complex64 words of the FP32 factor (HM_FP32_REFINED) */
+    HM_Q_STORAGE32 = 24,   /* complex64 words of the FP32 factor (HM_FP32_REFINED) */
+    HM_Q_ACA_PREALLOC = 25,/* complex words allocated for ACA factors by the last hm_fill (all attempts) */
+    HM_Q_ACA_RERUNS = 26,  /* blocks whose ACA was re-run because the rank model predicted too low */
+    HM_Q_RANK_PRED_ERR = 27,/* mean |predicted - achieved| of log(1 + ACA rank) in the last hm_fill */
+    /* QR + SVD recompressions since the last hm_fill or hm_factor began: */
+    HM_Q_TRUNC_BATCHES = 28,/* batched launches */
+    HM_Q_TRUNC_JOBS = 29,  /* low-rank sums recompressed */
+    HM_Q_TRUNC_MAXK = 30,  /* largest number of columns K of one sum */
+    HM_Q_TRUNC_WORK = 31,  /* sum of (m + n) K^2 over the sums */
+    HM_Q_T_TRUNC = 32,     /* wall seconds spent in them (they synchronise) */
+    HM_Q_ACA_SKIPPED = 33  /* ACA attempts the rank model skipped (predicted rank >= 1.25 x bound) */
 };
 
 const char *hm_version(void);
@@ -168,6 +179,52 @@ hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev);
 
 hm_status hm_query(hm_handle h, int what, double *out);
 const char *hm_last_error(hm_handle h);
+
+/* ---- learned ACA-rank predictor ---------------------------------------------
+ * The paper has no learned component.  A small MLP predicts, from the geometry of
+ * an admissible block, the rank ACA (Sec. III, ref. [22]) will reach.  The fill
+ * splits (or, on the leaf level, stores dense) without an attempt every block whose
+ * prediction is at least 1.25 times its rank bound, uses the prediction to size the
+ * other blocks' ACA buffers and to order the launch, and re-runs plain adaptive ACA
+ * with the full bound for every block whose prediction was too low.  Every low-rank
+ * block therefore still meets the ACA tolerance; only a wrongly skipped block changes
+ * the partition (it is split where plain ACA would have kept it).
+ *
+ * Features (HM_RANK_NFEAT = 8, float): log2|t|/10, log2|s|/10, diam(t)/(8 lambda),
+ * diam(s)/(8 lambda), dist(t,s)/(8 lambda), max(diam)/dist/4, Nc/10, -log10(tol)/10,
+ * with bounding-box diameters and distance (Eq. 21).  Target: log(1 + rank).
+ *
+ * Network: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = w3.h2 + b3 (FP32).
+ * Packed parameters (host float[hm_mlp_num_params]): W1 [nh][nin] row-major, b1 [nh],
+ * W2 [nh][nh], b2 [nh], w3 [nh], b3.  Loss (1/n) sum (y - t)^2; training is
+ * full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the device. */
+
+/* Samples of the last hm_fill: every conclusive ACA attempt (converged, or stopped at
+ * the block's real bound).  *n receives the count; feat_host [n][8] and target_host [n]
+ * may be NULL. */
+hm_status hm_rank_samples(hm_handle h, int *n, float *feat_host, float *target_host);
+/* Use model m (nin = 8) in the next hm_fill calls; NULL switches it off.  The handle
+ * does not own m. */
+hm_status hm_set_rank_model(hm_handle h, hm_mlp m);
+
+/* nin in 1..16, nh in 1..64; parameters start at zero (set them with hm_mlp_set_params). */
+hm_status hm_mlp_create(hm_mlp *m, int nin, int nh, void *cuda_stream);
+int hm_mlp_num_params(hm_mlp m);
+/* Copy parameters in (resets the Adam state) or out; host float arrays. */
+hm_status hm_mlp_set_params(hm_mlp m, const float *params);
+hm_status hm_mlp_get_params(hm_mlp m, float *params);
+/* y_dev[n] = network(x_dev[n][nin]); device float arrays. */
+hm_status hm_mlp_forward(hm_mlp m, int n, const float *x_dev, float *y_dev);
+/* Loss and its gradient for targets t_dev[n]; loss_host, grad_host (host, may be NULL).
+ * Synchronises. */
+hm_status hm_mlp_loss_grad(hm_mlp m, int n, const float *x_dev, const float *t_dev, double *loss_host,
+                           float *grad_host);
+/* steps full-batch Adam steps with learning rate lr; loss_host (may be NULL) receives the
+ * loss after the last step (synchronises). */
+hm_status hm_mlp_train(hm_mlp m, int n, const float *x_dev, const float *t_dev, int steps, float lr,
+                       double *loss_host);
+const char *hm_mlp_last_error(hm_mlp m);
+void hm_mlp_destroy(hm_mlp m);
 void hm_destroy(hm_handle h);
 
 /* ---- inspection (tests and diagnostics; all synchronise) ------------------- */

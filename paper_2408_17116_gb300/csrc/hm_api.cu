@@ -148,6 +148,33 @@ void storage(hm_handle_s *h, Block *root_unused, double &words, int &maxk, doubl
 
 }  // namespace
 
+// Geometric features of an admissible block (t, s) read by the rank model:
+// log2 of both sizes, both cluster diameters and their separation in wavelengths,
+// the separation ratio of Eq. 21, nodes per direction and the ACA tolerance.
+void rank_features(hm_handle_s *h, const Block *b, float *f)
+{
+    const Cluster &ct = h->clusters[b->t], &cs = h->clusters[b->s];
+    double dt = 0, ds = 0, g2 = 0;
+    for (int d = 0; d < 3; ++d) {
+        dt += (ct.bmax[d] - ct.bmin[d]) * (ct.bmax[d] - ct.bmin[d]);
+        ds += (cs.bmax[d] - cs.bmin[d]) * (cs.bmax[d] - cs.bmin[d]);
+        double g = std::max(0.0, std::max(ct.bmin[d] - cs.bmax[d], cs.bmin[d] - ct.bmax[d]));
+        g2 += g * g;
+    }
+    dt = std::sqrt(dt);
+    ds = std::sqrt(ds);
+    double dist = std::sqrt(g2);
+    const double lam = h->prm.k0 > 0 ? 2.0 * 3.14159265358979323846 / h->prm.k0 : 1.0;
+    f[0] = (float)(std::log2((double)b->nr) / 10.0);
+    f[1] = (float)(std::log2((double)b->nc) / 10.0);
+    f[2] = (float)(dt / lam / 8.0);
+    f[3] = (float)(ds / lam / 8.0);
+    f[4] = (float)(dist / lam / 8.0);
+    f[5] = (float)(std::max(dt, ds) / std::max(dist, 1e-300) / 4.0);
+    f[6] = (float)(h->nc / 10.0);
+    f[7] = (float)(-std::log10(h->tol) / 10.0);
+}
+
 extern "C" {
 
 const char *hm_version(void) { return HM_VERSION; }
@@ -244,6 +271,7 @@ hm_status hm_fill(hm_handle h)
             rebuild_block_tree(h);  // the adaptive ACA split below changes the tree
         }
         const int nc = h->nc, w = 2 * nc * nc;
+        h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         // near-field quadrature (A3)
         {
             Timer t(h->stream);
@@ -285,6 +313,11 @@ hm_status hm_fill(hm_handle h)
         // ACA of admissible leaves (A5).  A block whose ACA reaches its rank bound is split
         // into its four (still admissible) children and retried; at the leaf level it is
         // stored dense.  Dense blocks therefore only occur on the leaf level.
+        // With a rank model: a block whose predicted rank is at least 1.25 times its bound
+        // is split (or, on the leaf level, stored dense) without the doomed ACA attempt;
+        // otherwise the predicted rank sizes the block's buffers and orders the launch
+        // (largest predicted first), and a block whose ACA stops at a predicted bound below
+        // its real bound is re-run with the real bound (plain adaptive ACA).
         {
             Timer t(h->stream);
             std::vector<Block *> pending;
@@ -292,29 +325,111 @@ hm_status hm_fill(hm_handle h)
                 if (b->type == B_LR) pending.push_back(b);
             int cap = h->prm.aca_max_rank > 0 ? h->prm.aca_max_rank : HM_DEFAULT_RANK_CAP;
             h->aca_nonconv = 0;
+            h->aca_reruns = 0;
+            h->aca_skipped = 0;
+            h->aca_prealloc = 0;
+            h->rank_feat.clear();
+            h->rank_target.clear();
+            double pred_err = 0;
+            int npred = 0;
+            std::vector<int> rerun_bound;  // per pending block: 0 = first attempt, else the bound to use
+            rerun_bound.assign(pending.size(), 0);
             while (!pending.empty()) {
-                std::vector<LRDesc> descs;
-                for (Block *b : pending) {
-                    int kmax = std::min(cap, (int)((long long)b->nr * b->nc / (b->nr + b->nc)));
-                    kmax = std::max(kmax, 1);
-                    b->U = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nr * kmax);
-                    b->V = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nc * kmax);
-                    descs.push_back(LRDesc{b->r0, b->nr, b->c0, b->nc, b->U, b->V, kmax});
-                }
-                int *d_rf = (int *)dalloc(h, sizeof(int) * 2 * pending.size());
-                launch_aca(h, descs, d_rf, d_rf + pending.size());
-                std::vector<int> rf(2 * pending.size());
-                HM_CUDA(cudaMemcpyAsync(rf.data(), d_rf, sizeof(int) * rf.size(), cudaMemcpyDeviceToHost, h->stream));
-                HM_CUDA(cudaStreamSynchronize(h->stream));
-                dfree(h, d_rf);
-                std::vector<Block *> next;
-                for (size_t i = 0; i < pending.size(); ++i) {
+                const size_t np = pending.size();
+                std::vector<int> bound(np), kmaxv(np);
+                std::vector<float> feat((size_t)HM_RANK_NFEAT * np), pred(np, -1.0f);
+                for (size_t i = 0; i < np; ++i) {
                     Block *b = pending[i];
-                    if (!rf[pending.size() + i]) {
-                        b->k = rf[i];
+                    bound[i] = std::max(1, std::min(cap, (int)((long long)b->nr * b->nc / (b->nr + b->nc))));
+                    rank_features(h, b, &feat[HM_RANK_NFEAT * i]);
+                }
+                if (h->rank_model) mlp_predict_host(h->rank_model, (int)np, feat.data(), pred.data());
+                std::vector<size_t> order(np);
+                for (size_t i = 0; i < np; ++i) {
+                    order[i] = i;
+                    int km = bound[i];
+                    if (h->rank_model && !rerun_bound[i]) {
+                        double pk = std::exp((double)pred[i]) - 1.0;
+                        km = pk >= 1.25 * bound[i] ? 0  // predicted to fail: no attempt
+                                                   : std::min(bound[i], std::max(4, (int)std::ceil(1.25 * pk + 4.0)));
+                    } else if (rerun_bound[i]) {
+                        km = rerun_bound[i];
+                    }
+                    kmaxv[i] = km;
+                }
+                if (h->rank_model)
+                    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return kmaxv[a] > kmaxv[b]; });
+                std::vector<Block *> sorted(np);
+                std::vector<int> sb(np), sk(np), sr(np);
+                std::vector<float> sp(np);
+                std::vector<float> sf((size_t)HM_RANK_NFEAT * np);
+                for (size_t i = 0; i < np; ++i) {
+                    sorted[i] = pending[order[i]];
+                    sb[i] = bound[order[i]];
+                    sk[i] = kmaxv[order[i]];
+                    sr[i] = rerun_bound[order[i]];
+                    sp[i] = pred[order[i]];
+                    std::copy(&feat[HM_RANK_NFEAT * order[i]], &feat[HM_RANK_NFEAT * (order[i] + 1)],
+                              &sf[HM_RANK_NFEAT * i]);
+                }
+                pending.swap(sorted);
+                std::vector<LRDesc> descs;
+                std::vector<int> slot(np, -1);
+                for (size_t i = 0; i < np; ++i) {
+                    Block *b = pending[i];
+                    int kmax = sk[i];
+                    if (kmax == 0) {
+                        ++h->aca_skipped;
                         continue;
                     }
-                    ++h->aca_nonconv;
+                    b->U = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nr * kmax);
+                    b->V = (zc *)dalloc(h, sizeof(zc) * (size_t)b->nc * kmax);
+                    h->aca_prealloc += (double)kmax * (b->nr + b->nc);
+                    slot[i] = (int)descs.size();
+                    descs.push_back(LRDesc{b->r0, b->nr, b->c0, b->nc, b->U, b->V, kmax});
+                }
+                const size_t nd = descs.size();
+                std::vector<int> rf(2 * nd);
+                if (nd) {
+                    int *d_rf = (int *)dalloc(h, sizeof(int) * 2 * nd);
+                    launch_aca(h, descs, d_rf, d_rf + nd);
+                    HM_CUDA(cudaMemcpyAsync(rf.data(), d_rf, sizeof(int) * rf.size(), cudaMemcpyDeviceToHost,
+                                            h->stream));
+                    HM_CUDA(cudaStreamSynchronize(h->stream));
+                    dfree(h, d_rf);
+                }
+                std::vector<Block *> next;
+                std::vector<int> next_rerun;
+                for (size_t i = 0; i < pending.size(); ++i) {
+                    Block *b = pending[i];
+                    const bool skipped = slot[i] < 0;
+                    const bool hit = skipped || rf[nd + slot[i]] != 0;
+                    const int rank_i = skipped ? 0 : rf[slot[i]];
+                    if (!skipped && (!hit || sk[i] == sb[i])) {
+                        // training sample: the rank ACA needs (the bound when it was reached),
+                        // as log(1 + rank)
+                        h->rank_feat.insert(h->rank_feat.end(), &sf[HM_RANK_NFEAT * i], &sf[HM_RANK_NFEAT * (i + 1)]);
+                        h->rank_target.push_back((float)std::log(1.0 + (hit ? sb[i] : rank_i)));
+                        if (h->rank_model) {
+                            pred_err += std::fabs((double)sp[i] - h->rank_target.back());
+                            ++npred;
+                        }
+                    }
+                    if (!hit) {
+                        b->k = rank_i;
+                        continue;
+                    }
+                    if (!skipped && sk[i] < sb[i]) {
+                        // the prediction was too low: plain adaptive ACA with the real bound
+                        dfree(h, b->U);
+                        dfree(h, b->V);
+                        b->U = b->V = nullptr;
+                        ++h->aca_reruns;
+                        next.push_back(b);
+                        next_rerun.push_back(sb[i]);
+                        continue;
+                    }
+                    if (!skipped) ++h->aca_nonconv;
                     dfree(h, b->U);
                     dfree(h, b->V);
                     b->U = b->V = nullptr;
@@ -336,13 +451,16 @@ hm_status hm_fill(hm_handle h)
                                 ch->type = B_LR;
                                 b->ch[2 * a + c] = ch;
                                 next.push_back(ch);
+                                next_rerun.push_back(0);
                             }
                     } else {
                         b->type = B_DENSE;
                     }
                 }
                 pending.swap(next);
+                rerun_bound.swap(next_rerun);
             }
+            h->rank_pred_err = npred ? pred_err / npred : 0.0;
             rebuild_leaves(h);
             h->t_aca = t.stop();
         }
@@ -380,11 +498,22 @@ hm_status hm_factor(hm_handle h)
     return guard(h, [&] {
         if (h->state != 2) throw HmError{HM_ERR_STATE, "hm_factor requires a filled, unfactored matrix"};
         h->flops_factor = 0;
+        h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         if (h->prm.precision == HM_FP32_REFINED) {
             // the FP64 H-matrix stays unfactored: it is the refinement operator
             Timer t(h->stream);
             free_tree(h, h->blocks32);
+            h->dirty32.clear();
             h->root32 = clone_tree<cf>(h, h->root, h->blocks32);
+            // the factor only needs factor_tol: recompress the copied low-rank leaves first
+            std::vector<Block32 *> lr;
+            std::vector<int> ranks;
+            for (Block32 *b : h->blocks32)
+                if (b->type == B_LR && b->k > 0) {
+                    lr.push_back(b);
+                    ranks.push_back(b->k);
+                }
+            batched_truncate<cf>(h, lr, ranks, h->factor_tol);
             hlu_factor<cf>(h, h->root32, h->factor_tol);
             h->t_factor = t.stop();
             h->state = 3;
@@ -395,6 +524,7 @@ hm_status hm_factor(hm_handle h)
             h->copy_root = clone_tree<zc>(h, h->root, h->copy_blocks);
         }
         Timer t(h->stream);
+        h->dirty64.clear();
         hlu_factor<zc>(h, h->root, h->tol);
         h->t_factor = t.stop();
         h->state = 3;
@@ -604,6 +734,15 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_MEAN_RANK: *out = meank; break;
         case HM_Q_STORAGE_FACTOR: *out = words; break;
         case HM_Q_REFINE_ITERS: *out = h->refine_iters; break;
+        case HM_Q_ACA_PREALLOC: *out = h->aca_prealloc; break;
+        case HM_Q_ACA_RERUNS: *out = h->aca_reruns; break;
+        case HM_Q_RANK_PRED_ERR: *out = h->rank_pred_err; break;
+        case HM_Q_TRUNC_BATCHES: *out = h->tr_batches; break;
+        case HM_Q_TRUNC_JOBS: *out = h->tr_jobs; break;
+        case HM_Q_TRUNC_MAXK: *out = h->tr_maxk; break;
+        case HM_Q_TRUNC_WORK: *out = h->tr_work; break;
+        case HM_Q_T_TRUNC: *out = h->tr_seconds; break;
+        case HM_Q_ACA_SKIPPED: *out = h->aca_skipped; break;
         case HM_Q_REFINE_RES: *out = h->refine_res; break;
         case HM_Q_STORAGE32: {
             double w32 = 0;
@@ -620,6 +759,25 @@ hm_status hm_query(hm_handle h, int what, double *out)
 }
 
 const char *hm_last_error(hm_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+hm_status hm_rank_samples(hm_handle h, int *n, float *feat_host, float *target_host)
+{
+    return guard(h, [&] {
+        if (!n) throw HmError{HM_ERR_ARG, "null count"};
+        if (h->state < 2) throw HmError{HM_ERR_STATE, "rank samples exist after hm_fill"};
+        *n = (int)h->rank_target.size();
+        if (feat_host) std::copy(h->rank_feat.begin(), h->rank_feat.end(), feat_host);
+        if (target_host) std::copy(h->rank_target.begin(), h->rank_target.end(), target_host);
+    });
+}
+
+hm_status hm_set_rank_model(hm_handle h, hm_mlp m)
+{
+    return guard(h, [&] {
+        if (m && mlp_nin(m) != HM_RANK_NFEAT) throw HmError{HM_ERR_ARG, "rank model must have 8 inputs"};
+        h->rank_model = m;
+    });
+}
 
 void hm_destroy(hm_handle h)
 {

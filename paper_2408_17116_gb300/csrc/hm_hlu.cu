@@ -82,18 +82,43 @@ static void collect_pending(BlockT<Z> *b, std::vector<BlockT<Z> *> &out)
 {
     if (b->type == B_HIER) {
         for (int i = 0; i < 4; ++i) collect_pending(b->ch[i], out);
-    } else if (b->type == B_LR && b->pend_k > 0) {
+    } else if (b->type == B_LR && b->pend_k > 0 && !b->in_batch) {
+        b->in_batch = true;
         out.push_back(b);
     }
 }
 
+template <class Z>
+std::vector<BlockT<Z> *> &dirty_list(hm_handle_s *h);
+template <>
+std::vector<Block *> &dirty_list<zc>(hm_handle_s *h)
+{
+    return h->dirty64;
+}
+template <>
+std::vector<Block32 *> &dirty_list<cf>(hm_handle_s *h)
+{
+    return h->dirty32;
+}
+
 // Recompress, in one batch, every low-rank block of b's subtree that has pending
-// updates: [U | Up_1 | ...] [V | Vp_1 | ...]^H -> truncated U' V'^H.
+// updates, together with every block queued as dirty anywhere in the matrix:
+// [U | Up_1 | ...] [V | Vp_1 | ...]^H -> truncated U' V'^H.
 template <class Z>
 void flush(hm_handle_s *h, BlockT<Z> *b)
 {
     std::vector<BlockT<Z> *> list;
     collect_pending(b, list);
+    std::vector<BlockT<Z> *> &dl = dirty_list<Z>(h);
+    for (BlockT<Z> *d : dl) {
+        d->dirty = false;
+        if (d->pend_k > 0 && !d->in_batch) {
+            d->in_batch = true;
+            list.push_back(d);
+        }
+    }
+    dl.clear();
+    for (BlockT<Z> *c : list) c->in_batch = false;
     if (list.empty()) return;
     std::vector<int> ranks;
     for (BlockT<Z> *c : list) {
@@ -147,7 +172,17 @@ static void add_lr(hm_handle_s *h, BlockT<Z> *C, MVT<Z> U, MVT<Z> V, Z alpha)
         C->pv.push_back(Vp);
         C->pk.push_back(k);
         C->pend_k += k;
-        if (C->k + C->pend_k > std::max(256, std::min(C->nr, C->nc))) flush(h, C);
+        // once the pending columns reach the current rank (at least 32) the block is
+        // queued for the next batched recompression; beyond four times that bound it is
+        // recompressed at once
+        if (C->pend_k >= std::max(32, C->k)) {
+            if (C->k + C->pend_k > 4 * std::max(64, C->k)) {
+                flush(h, C);
+            } else if (!C->dirty) {
+                C->dirty = true;
+                dirty_list<Z>(h).push_back(C);
+            }
+        }
         break;
     }
     case B_HIER:

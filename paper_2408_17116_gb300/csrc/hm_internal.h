@@ -62,6 +62,8 @@ struct BlockT {
     std::vector<C *> pu, pv;
     std::vector<int> pk;
     int pend_k = 0;
+    bool dirty = false;     // queued for the next batched recompression
+    bool in_batch = false;  // scratch flag while a batch is assembled
 };
 typedef BlockT<zc> Block;
 typedef BlockT<cf> Block32;
@@ -105,20 +107,39 @@ struct hm_handle_s {
     std::vector<Block *> leaves;
     Block *copy_root = nullptr;   // unfactored copy (keep_matrix)
     std::vector<Block *> copy_blocks;
+    // low-rank leaves whose pending updates reached the recompression threshold; they are
+    // recompressed together with the next batch that has to run
+    std::vector<Block *> dirty64;
+    std::vector<Block32 *> dirty32;
     Block32 *root32 = nullptr;    // FP32 factor (precision HM_FP32_REFINED)
     std::vector<Block32 *> blocks32;
+    // rank model (learned ACA-rank predictor) and the samples of the last fill
+    hm_mlp rank_model = nullptr;
+    std::vector<float> rank_feat, rank_target;  // [n][HM_RANK_NFEAT], log(1 + rank)
+    double aca_prealloc = 0;      // complex words allocated for ACA factors by the last fill
+    int aca_reruns = 0;           // blocks re-run because the predicted rank was too low
+    int aca_skipped = 0;          // attempts skipped because the model predicted failure
+    double rank_pred_err = 0;     // mean |predicted - achieved| log(1 + rank) of the last fill
     double factor_tol = 1e-5;     // truncation tolerance of the FP32 factor
     int refine_iters = 0;         // refinement steps taken by the last solve
     double refine_res = 0;        // final relative residual of the last solve (max over RHS)
     // statistics
     double t_geom = 0, t_near = 0, t_dense = 0, t_aca = 0, t_trunc = 0, t_factor = 0, t_solve = 0;
     double flops_factor = 0;
+    // recompression statistics (reset by hm_fill and hm_factor)
+    double tr_batches = 0, tr_jobs = 0, tr_maxk = 0, tr_work = 0, tr_seconds = 0;
     long long launches = 0;
     int aca_nonconv = 0;
     unsigned long long near_points = 0;
     double tol = 1e-7;
     double cur_tol = 1e-7;       // truncation tolerance of the factorisation in progress
 };
+
+// ---- hm_mlp.cu ----
+#define HM_RANK_NFEAT 8
+void mlp_predict_host(hm_mlp m, int n, const float *feat_host, float *pred_host);
+int mlp_nin(hm_mlp m);
+void rank_features(hm_handle_s *h, const Block *b, float *f);  // hm_api.cu
 
 // ---- device memory (stream-ordered pool) ----
 void *dalloc(hm_handle_s *h, size_t bytes);

@@ -5,6 +5,7 @@
 //
 // On GB300 FP64 runs on the CUDA-core FP64 pipe; these kernels are bound by it.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 
 #include "hm_internal.h"
@@ -59,6 +60,15 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs<C> g)
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = cmk<C>(0, 0);
+    // warp-uniform masks of the 16-row / 16-column groups that hold outputs: partial
+    // tiles skip the products of padding (on GB300 the FP64 pipe is the bound)
+    const int wy0 = j0 + ((tid >> 5) << 1);  // first column of this warp's threads
+    bool vx[4], vy[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        vx[q] = i0 + 16 * q < g.m;
+        vy[q] = wy0 + 16 * q < g.n;
+    }
     for (int p0 = kb; p0 < ke; p0 += GB_K) {
         // load 64 x 8 of A and 8 x 64 of B: 512 elements each, 2 per thread
 #pragma unroll
@@ -80,9 +90,12 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs<C> g)
                 b[q] = Bs[pp][ty + 16 * q];
             }
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < 4; ++x) {
+                if (!vx[x]) continue;
 #pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = zfma(a[x], b[y], acc[x][y]);
+                for (int y = 0; y < 4; ++y)
+                    if (vy[y]) acc[x][y] = zfma(a[x], b[y], acc[x][y]);
+            }
         }
         __syncthreads();
     }
@@ -569,8 +582,8 @@ struct SVDDesc {
 
 // Relative size of an off-diagonal inner product below which a Jacobi rotation is skipped.
 template <class R> __device__ __forceinline__ R jacobi_eps();
-template <> __device__ __forceinline__ double jacobi_eps<double>() { return 1e-15; }
-template <> __device__ __forceinline__ float jacobi_eps<float>() { return 1e-7f; }
+template <> __device__ __forceinline__ double jacobi_eps<double>() { return 1e-14; }
+template <> __device__ __forceinline__ float jacobi_eps<float>() { return 1e-6f; }
 
 #define SVD_T 512
 #define SVD_QMAX 4096
@@ -583,20 +596,22 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc<C> *__restrict__ de
     const int p = d.p, q = d.q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = SVD_T / 32;
     __shared__ int s_rot;
-    extern __shared__ int perm[];  // [q rounded up to even]
     for (int e = tid; e < q * q; e += SVD_T) {
         int i = e % q, j = e / q;
         d.Y[(size_t)j * q + i] = cmk<C>(i == j ? 1 : 0, 0);
     }
     const int qe = (q + 1) & ~1;  // even count (a dummy column when q is odd)
-    for (int i = tid; i < qe; i += SVD_T) perm[i] = i;
     __syncthreads();
+    // Round-robin ordering: position 0 holds column 0; in round r position k >= 1 holds
+    // column 1 + ((k - 1 - r) mod (qe - 1)); round r pairs positions pr and qe - 1 - pr.
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < qe - 1; ++round) {
             for (int pr = warp; pr < qe / 2; pr += nw) {
-                int a = perm[pr], b = perm[qe - 1 - pr];
+                const int pa = pr, pb = qe - 1 - pr;
+                int a = pa == 0 ? 0 : 1 + ((pa - 1 - round) % (qe - 1) + (qe - 1)) % (qe - 1);
+                int b = 1 + ((pb - 1 - round) % (qe - 1) + (qe - 1)) % (qe - 1);
                 if (a >= q || b >= q) continue;
                 if (a > b) {
                     int t = a;
@@ -638,13 +653,6 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc<C> *__restrict__ de
                 }
             }
             __syncthreads();
-            // rotate the round-robin order (position 0 fixed)
-            if (tid == 0) {
-                int last = perm[qe - 1];
-                for (int i = qe - 1; i > 1; --i) perm[i] = perm[i - 1];
-                perm[1] = last;
-            }
-            __syncthreads();
         }
         if (!s_rot) break;
         __syncthreads();
@@ -656,18 +664,16 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc<C> *__restrict__ de
         if (lane == 0) d.S[j] = sqrt(s);
     }
     __syncthreads();
-    if (tid == 0) {
-        // insertion sort of indices by decreasing S (q is small)
-        for (int j = 0; j < q; ++j) d.ord[j] = j;
-        for (int j = 1; j < q; ++j) {
-            int v = d.ord[j];
-            int i = j - 1;
-            while (i >= 0 && d.S[d.ord[i]] < d.S[v]) {
-                d.ord[i + 1] = d.ord[i];
-                --i;
-            }
-            d.ord[i + 1] = v;
+    // order by decreasing S (ties: lower index first): each column's rank is the number
+    // of columns that precede it
+    for (int j = tid; j < q; j += SVD_T) {
+        const R sj = d.S[j];
+        int rank = 0;
+        for (int i = 0; i < q; ++i) {
+            const R si = d.S[i];
+            rank += (si > sj) || (si == sj && i < j);
         }
+        d.ord[rank] = j;
     }
 }
 
@@ -752,7 +758,7 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
     if (qmax > SVD_QMAX) throw HmError{HM_ERR_NUMERIC, "recompression core too large: " + std::to_string(qmax)};
     SVDDesc<C> *d_sd = (SVDDesc<C> *)dalloc(h, sizeof(SVDDesc<C>) * sd.size());
     HM_CUDA(cudaMemcpyAsync(d_sd, sd.data(), sizeof(SVDDesc<C>) * sd.size(), cudaMemcpyHostToDevice, h->stream));
-    k_svd<C><<<(unsigned)sd.size(), SVD_T, sizeof(int) * (qmax + 2), h->stream>>>(d_sd);
+    k_svd<C><<<(unsigned)sd.size(), SVD_T, 0, h->stream>>>(d_sd);
     HM_CHECK_LAUNCH();
     count_launch(h);
     HM_CUDA(cudaStreamSynchronize(h->stream));
@@ -855,6 +861,7 @@ template <class C>
 void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std::vector<int> &ranks, double tol)
 {
     const size_t CH = 512;  // jobs per batch (bounds the workspace)
+    auto t0 = std::chrono::steady_clock::now();
     for (size_t s = 0; s < blks.size(); s += CH) {
         size_t e = std::min(blks.size(), s + CH);
         std::vector<TruncJob<C>> jobs;
@@ -875,6 +882,12 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
             idx.push_back(i);
         }
         if (jobs.empty()) continue;
+        h->tr_batches += 1;
+        h->tr_jobs += (double)jobs.size();
+        for (auto &J : jobs) {
+            h->tr_maxk = std::max(h->tr_maxk, (double)J.K);
+            h->tr_work += ((double)J.m + J.n) * J.K * J.K;
+        }
         trunc_stage1(h, jobs);
         std::vector<std::vector<double>> S;
         std::vector<std::vector<int>> ord;
@@ -890,6 +903,7 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
             b->k = kk;
         }
     }
+    h->tr_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 // ---------------------------------------------------------------------------

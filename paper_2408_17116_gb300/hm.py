@@ -18,13 +18,18 @@ STATUS = {0: "HM_OK", 1: "HM_ERR_ARG", 2: "HM_ERR_STATE", 3: "HM_ERR_CUDA", 4: "
 Q = dict(N=0, NNODE=1, NPATCH=2, NEAR_PAIRS=3, DENSE_BLOCKS=4, LR_BLOCKS=5, CR=6, MAX_RANK=7,
          T_GEOMETRY=8, T_NEAR=9, T_DENSE=10, T_ACA=11, T_FACTOR=12, T_SOLVE=13, FLOPS_FACTOR=14,
          STORAGE=15, ACA_NONCONV=16, LAUNCHES=17, NEAR_QPOINTS=18, MEAN_RANK=19, STORAGE_FACTOR=20,
-         T_RECOMPRESS=21, REFINE_ITERS=22, REFINE_RES=23, STORAGE32=24)
+         T_RECOMPRESS=21, REFINE_ITERS=22, REFINE_RES=23, STORAGE32=24, ACA_PREALLOC=25, ACA_RERUNS=26,
+         RANK_PRED_ERR=27, TRUNC_BATCHES=28, TRUNC_JOBS=29, TRUNC_MAXK=30, TRUNC_WORK=31, T_TRUNC=32,
+         ACA_SKIPPED=33)
+RANK_NFEAT = 8
 HM_FP64, HM_FP32_REFINED = 0, 1
 
 EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor", "hm_solve",
            "hm_solve_host", "hm_farfield", "hm_matvec", "hm_query", "hm_last_error", "hm_destroy",
            "hm_get_nodes_host", "hm_get_near_pairs_host", "hm_get_near_block_host", "hm_entries_host",
-           "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host")
+           "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host", "hm_rank_samples",
+           "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
+           "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy")
 
 
 class hm_params(ctypes.Structure):
@@ -78,8 +83,21 @@ def load(path=SO):
     L.hm_get_perm_host.argtypes = [P, P]
     L.hm_get_blocks_host.argtypes = [P, ctypes.POINTER(I), P]
     L.hm_get_block_dense_host.argtypes = [P, I, P]
+    L.hm_rank_samples.argtypes = [P, ctypes.POINTER(I), P, P]
+    L.hm_set_rank_model.argtypes = [P, P]
+    L.hm_mlp_create.argtypes = [ctypes.POINTER(P), I, I, P]
+    L.hm_mlp_num_params.argtypes = [P]
+    L.hm_mlp_set_params.argtypes = [P, P]
+    L.hm_mlp_get_params.argtypes = [P, P]
+    L.hm_mlp_forward.argtypes = [P, I, P, P]
+    L.hm_mlp_loss_grad.argtypes = [P, I, P, P, ctypes.POINTER(D), P]
+    L.hm_mlp_train.argtypes = [P, I, P, P, I, ctypes.c_float, ctypes.POINTER(D)]
+    L.hm_mlp_last_error.restype = ctypes.c_char_p
+    L.hm_mlp_last_error.argtypes = [P]
+    L.hm_mlp_destroy.argtypes = [P]
+    L.hm_mlp_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("hm_version", "hm_last_error", "hm_destroy"):
+        if name not in ("hm_version", "hm_last_error", "hm_destroy", "hm_mlp_last_error", "hm_mlp_destroy"):
             getattr(L, name).restype = I
     _lib = L
     return L
@@ -226,3 +244,80 @@ class Solver:
         out = np.empty((info[4], info[2]), dtype=np.complex128)  # column-major nr x nc -> (nc, nr) C-order
         self._check(self.L.hm_get_block_dense_host(self.h, int(b), _np_ptr(out)))
         return out.T
+
+    def rank_samples(self):
+        """(features [n][8] float32, log(1 + ACA rank) [n] float32) of the last hm_fill."""
+        n = ctypes.c_int()
+        self._check(self.L.hm_rank_samples(self.h, ctypes.byref(n), None, None))
+        f = np.empty((n.value, RANK_NFEAT), dtype=np.float32)
+        t = np.empty(n.value, dtype=np.float32)
+        self._check(self.L.hm_rank_samples(self.h, ctypes.byref(n), _np_ptr(f), _np_ptr(t)))
+        return f, t
+
+    def set_rank_model(self, mlp):
+        self._rank_model = mlp  # keeps the model alive while the handle may use it
+        self._check(self.L.hm_set_rank_model(self.h, mlp.m if mlp is not None else None))
+
+
+class MLP:
+    """One hm_mlp: the learned ACA-rank predictor (include/hm.h)."""
+
+    def __init__(self, nin=RANK_NFEAT, nh=32, stream=None):
+        import torch
+        self.torch = torch
+        self.L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.m = ctypes.c_void_p()
+        st = self.L.hm_mlp_create(ctypes.byref(self.m), int(nin), int(nh), ctypes.c_void_p(stream))
+        if st != HM_OK:
+            raise HmError(st, "hm_mlp_create")
+        self.nin, self.nh = int(nin), int(nh)
+        self.np = self.L.hm_mlp_num_params(self.m)
+
+    def _check(self, st):
+        if st != HM_OK:
+            raise HmError(st, self.L.hm_mlp_last_error(self.m).decode())
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.L.hm_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        assert p.size == self.np
+        self._check(self.L.hm_mlp_set_params(self.m, _np_ptr(p)))
+
+    def get_params(self):
+        p = np.empty(self.np, dtype=np.float32)
+        self._check(self.L.hm_mlp_get_params(self.m, _np_ptr(p)))
+        return p
+
+    def forward(self, x):
+        x = x.contiguous()
+        y = self.torch.empty(x.shape[0], dtype=self.torch.float32, device=x.device)
+        self._check(self.L.hm_mlp_forward(self.m, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def loss_grad(self, x, t):
+        x, t = x.contiguous(), t.contiguous()
+        loss = ctypes.c_double()
+        g = np.empty(self.np, dtype=np.float32)
+        self._check(self.L.hm_mlp_loss_grad(self.m, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(t.data_ptr()), ctypes.byref(loss), _np_ptr(g)))
+        return loss.value, g
+
+    def train(self, x, t, steps, lr):
+        x, t = x.contiguous(), t.contiguous()
+        loss = ctypes.c_double()
+        self._check(self.L.hm_mlp_train(self.m, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(t.data_ptr()), int(steps), float(lr), ctypes.byref(loss)))
+        return loss.value

@@ -71,3 +71,21 @@ def workload(name):
 
 
 WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d2_m2_nc6", "ellipsoid_small")
+
+
+def mlp_init(nin, nh, seed=SEED):
+    """Seeded initial parameters of the rank-predictor MLP (packed as the library expects:
+    W1, b1, W2, b2, w3, b3): weights uniform in +-1/sqrt(fan_in), biases zero."""
+    g = np.random.Generator(np.random.Philox(seed + 7))
+    W1 = g.uniform(-1, 1, (nh, nin)) / np.sqrt(nin)
+    W2 = g.uniform(-1, 1, (nh, nh)) / np.sqrt(nh)
+    w3 = g.uniform(-1, 1, nh) / np.sqrt(nh)
+    return np.concatenate([W1.ravel(), np.zeros(nh), W2.ravel(), np.zeros(nh), w3, [0.0]]).astype(np.float32)
+
+
+def mlp_toy_data(n, nin, seed=SEED):
+    """Seeded synthetic regression data for the MLP kernels' parity tests."""
+    g = np.random.Generator(np.random.Philox(seed + 11))
+    X = g.uniform(-1, 1, (n, nin)).astype(np.float32)
+    t = (np.sin(X @ np.linspace(0.5, 1.5, nin)) + 0.1 * X[:, 0] ** 2).astype(np.float32)
+    return X, t

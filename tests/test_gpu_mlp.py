@@ -1,0 +1,116 @@
+"""The learned ACA-rank predictor on the GPU, through the C-ABI: forward, loss,
+gradients and Adam steps against the FP64 oracle (oracle/mlp.py); training on the
+ranks the method itself produces; and what the trained model gains in the fill
+(ACA buffers preallocated) while the H-matrix stays the one plain ACA gives.
+
+Tolerances: the kernels run in FP32, so values and gradients are compared at
+2e-5 relative to the largest magnitude (a few FP32 roundings through two tanh
+layers of width 32)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2408_17116_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2408_17116_gb300 import build, hm  # noqa: E402
+
+build.build()
+NIN, NH = 8, 32
+
+
+def _setup(n=1000):
+    X, t = workloads.mlp_toy_data(n, NIN)
+    p = workloads.mlp_init(NIN, NH)
+    m = hm.MLP(NIN, NH)
+    m.set_params(p)
+    return m, p, X, t
+
+
+def test_forward_matches_oracle():
+    m, p, X, t = _setup(777)  # ragged: not a multiple of the 128-thread CTA
+    y = m.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    yo, _, _ = omlp.forward(p, X, NIN, NH)
+    assert np.max(np.abs(y - yo)) <= 2e-5 * np.max(np.abs(yo))
+    assert np.array_equal(m.get_params(), p)
+
+
+def test_loss_and_gradient_match_oracle():
+    m, p, X, t = _setup(1000)
+    L, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(t, device="cuda"))
+    Lo, go = omlp.loss_grad(p, X, t, NIN, NH)
+    assert abs(L - Lo) <= 2e-5 * Lo
+    assert np.max(np.abs(g - go)) <= 2e-5 * np.max(np.abs(go))
+
+
+def test_adam_steps_match_oracle_and_reduce_the_loss():
+    m, p, X, t = _setup(500)
+    Xd, td = torch.tensor(X, device="cuda"), torch.tensor(t, device="cuda")
+    L5 = m.train(Xd, td, 5, 1e-2)
+    po = p.astype(np.float64)
+    opt = omlp.Adam(po.size, 1e-2)
+    for _ in range(5):
+        _, g = omlp.loss_grad(po, X, t, NIN, NH)
+        po = opt.step(po, g)
+    assert np.max(np.abs(m.get_params() - po)) <= 1e-4 * np.max(np.abs(po))
+    assert abs(L5 - omlp.loss(po, X, t, NIN, NH)) <= 1e-3 * L5
+    L0 = omlp.loss(p, X, t, NIN, NH)
+    L300 = m.train(Xd, td, 300, 1e-2)
+    assert L300 < 0.2 * L0
+
+
+def _fill(wl, model=None):
+    s = hm.Solver()
+    s.hm_build_geometry(wl["bodies"], wl["ms"], wl["nc"], wl["k"], wl["leaf"], wl["eta"], wl["aca_tol"],
+                        keep_matrix=True)
+    if model is not None:
+        s.set_rank_model(model)
+    s.hm_fill()
+    return s
+
+
+def test_rank_model_trained_on_method_ranks_gains_over_plain_aca():
+    # training data: the ranks plain ACA reaches on spheres and ellipsoids of 3.5-5
+    # wavelengths (4,800 unknowns each, fill only)
+    base = dict(workloads.workload("sphere_d8_m4_nc10"), ms=[2], nc=10)
+    bodies = [workloads.body(semi=(1.75,) * 3), workloads.body(semi=(2.5, 2.0, 1.5)),
+              workloads.body(semi=(2.25,) * 3), workloads.body(semi=(2.4, 1.6, 2.0))]
+    feats, targs = [], []
+    for bd in bodies:
+        s = _fill(dict(base, bodies=bd[None]))
+        f, t = s.rank_samples()
+        feats.append(f)
+        targs.append(t)
+        s.close()
+    X = np.concatenate(feats)
+    t = np.concatenate(targs)
+    assert X.shape[0] > 200 and np.all(t > 0)
+    m = hm.MLP(NIN, NH)
+    m.set_params(workloads.mlp_init(NIN, NH))
+    Xd, td = torch.tensor(X, device="cuda"), torch.tensor(t, device="cuda")
+    L = m.train(Xd, td, 2000, 3e-3)
+    assert L < 0.1 * np.var(t)
+    # a body the model has not seen (a 4-wavelength sphere): doomed attempts skipped,
+    # buffers sized by the prediction, the same operator to within the ACA tolerance
+    wl = dict(base, bodies=workloads.body(semi=(2.0,) * 3)[None])
+    plain = _fill(wl)
+    learned = _fill(wl, m)
+    assert plain.hm_query("LR_BLOCKS") > 100
+    assert learned.hm_query("ACA_SKIPPED") > 0
+    assert learned.hm_query("ACA_PREALLOC") < 0.6 * plain.hm_query("ACA_PREALLOC")
+    assert learned.hm_query("RANK_PRED_ERR") < 0.5
+    bp, bl = plain.blocks(), learned.blocks()
+    same = len(bp) == len(bl) and np.array_equal(bp, bl)
+    rng = np.random.default_rng(2)
+    xr = rng.standard_normal((1, plain.N)) + 1j * rng.standard_normal((1, plain.N))
+    yp = plain.hm_matvec(torch.tensor(xr, device="cuda")).cpu().numpy()
+    yl = learned.hm_matvec(torch.tensor(xr, device="cuda")).cpu().numpy()
+    if same:
+        assert np.array_equal(yp, yl)  # the same partition: the identical H-matrix
+    else:
+        assert np.linalg.norm(yp - yl) <= 10 * wl["aca_tol"] * np.linalg.norm(yp)
