@@ -29,8 +29,11 @@ import numpy as np  # noqa: E402
 
 METRIC = "fill+factor+solve unknowns/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 on GB300: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s)
+# ALU peaks derived from unit counts and the maximum SM clock (2.07 GHz): FP64 on GB300,
+# 152 SMs x 2 FP64 FMA/clk x 2 flops (nominal 1.25 TFLOP/s); FP32 CUDA cores,
+# 152 SMs x 128 FP32 FMA/clk x 2 flops.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 flops per near-field kernel evaluation: geometry map (2 tan, sqrt, rcp, ~60 fma),
 # distance (sqrt), sincos, g(R) (~12), two cross products (12), four dots (12), Chebyshev
 # recurrence of one axis (2 Nc) and the moment accumulation (4 components x 2 x Nc) --
@@ -108,12 +111,12 @@ def cpu_baseline(wl, budget_s=20.0):
     o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
     N = o.N
     rng = np.random.default_rng(0)
-    R = 32
+    R = 16
     rows = np.sort(rng.choice(N, R, replace=False))
     t = time.perf_counter()
     A = o.matrix_rows(rows)
     t_rows = time.perf_counter() - t
-    ns = min(N, 2048)
+    ns = min(N, 1024)
     idx = np.sort(rng.choice(N, ns, replace=False))
     Bm = o.matrix_rows(idx)[:, idx]  # a principal submatrix of the same operator
     t = time.perf_counter()
@@ -179,14 +182,16 @@ def one_step(s, wl, dirs, host=False, precision="fp32r"):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="sphere_d8_m4_nc10")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32r", choices=sorted(PRECISION),
                     help="fp32r: FP32 H-LU + FP64 refinement (default); fp64: the plain FP64 H-LU")
-    ap.add_argument("--no-compare", action="store_true", help="skip the one-step run of the other precision")
+    ap.add_argument("--no-compare", action="store_true", help="skip the one-step runs of both precisions")
+    ap.add_argument("--compare-workload", default="sphere_d2_m2_nc6",
+                    help="workload of the FP32-refined vs plain-FP64 comparison (one step each)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,8 +222,16 @@ def main():
         torch.cuda.synchronize()
 
     prec = args.precision
-    for _ in range(args.warmup):
+
+    def progress(msg):
+        if rank == 0:
+            print("[bench] %s" % msg, file=sys.stderr, flush=True)
+
+    for i in range(args.warmup):
+        t = time.perf_counter()
         one_step(s, wl, dirs, precision=prec)
+        progress("warm-up %d: %.1f s (factor %.1f s, solve %.1f s, %d refinement steps)" % (
+            i, time.perf_counter() - t, s.hm_query("T_FACTOR"), s.hm_query("T_SOLVE"), s.hm_query("REFINE_ITERS")))
     barrier()
     L0 = s.hm_query("LAUNCHES")
     clk = ClockSampler(local)
@@ -226,6 +239,8 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     phases = {k: 0.0 for k in ("T_GEOMETRY", "T_NEAR", "T_ACA", "T_RECOMPRESS", "T_DENSE", "T_FACTOR", "T_SOLVE")}
     near_pts = 0.0
+    kern = {k: 0.0 for k in ("KQR_SECONDS", "KQR_FLOPS", "KQR_LAUNCHES", "KCORE_SECONDS", "KCORE_FLOPS",
+                             "KCORE_LAUNCHES")}
     barrier()
     ev0.record(stream)
     for _ in range(args.steps):
@@ -233,10 +248,13 @@ def main():
         for k in phases:
             phases[k] += s.hm_query(k)
         near_pts += s.hm_query("NEAR_QPOINTS")
+        for k in kern:  # counters of the last reset: hm_factor's recompressions
+            kern[k] += s.hm_query(k)
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
+    progress("timed: %.1f ms per step" % ms)
     launches = int(s.hm_query("LAUNCHES") - L0)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -253,16 +271,41 @@ def main():
     xh, rcs_h = one_step(s, wl, dirs, host=True, precision=prec)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t
+    progress("e2e: %.1f s" % e2e_s)
     nrhs = wl["kdirs"].shape[0]
     h2d = 152 * len(wl["ms"]) + 64 + 48 * nrhs + 24 * dirs.shape[0]  # bodies, params, waves, directions
     d2h = 16 * N * nrhs + 8 * nrhs * dirs.shape[0]
-    # roofline of the near-field quadrature kernel (FP64 ALU bound), per launch
+    # rooflines of the kernels timed live with CUDA events (per launch: algorithmic flops of
+    # one launch / its average device time); the one with the most device time per step is
+    # reported as "roofline", the others under "kernels"
     per = {k: v / args.steps for k, v in phases.items()}
     near_flops = (near_pts / args.steps) * NEAR_FLOPS_PER_POINT(wl["nc"])
-    near_tflops = near_flops / per["T_NEAR"] / 1e12 if per["T_NEAR"] > 0 else 0.0
-    roof = {"kernel": "k_near (self/near CBIE quadrature)", "bound": "alu", "achieved": near_tflops,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": near_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    cands = []
+    if per["T_NEAR"] > 0:
+        a = near_flops / per["T_NEAR"] / 1e12
+        cands.append({"kernel": "k_near (self/near CBIE quadrature, FP64)", "bound": "alu", "achieved": a,
+                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_PEAK_TFLOPS, "traffic": None,
+                      "launches_per_step": 1, "seconds_per_step": per["T_NEAR"],
+                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"})
+    fp32 = prec == "fp32r"
+    pk = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    src = ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz" if fp32
+           else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz")
+    if kern["KQR_SECONDS"] > 0:
+        a = kern["KQR_FLOPS"] / kern["KQR_SECONDS"] / 1e12
+        cands.append({"kernel": "k_qr<%s> (Householder QR of low-rank factors in the H-LU recompression)"
+                      % ("float2" if fp32 else "double2"), "bound": "alu", "achieved": a, "peak": pk,
+                      "unit": "TFLOP/s", "frac": a / pk, "traffic": None,
+                      "launches_per_step": kern["KQR_LAUNCHES"] / args.steps,
+                      "seconds_per_step": kern["KQR_SECONDS"] / args.steps, "peak_source": src})
+    if kern["KCORE_SECONDS"] > 0 and kern["KCORE_FLOPS"] > 0:
+        a = kern["KCORE_FLOPS"] / kern["KCORE_SECONDS"] / 1e12
+        cands.append({"kernel": "k_qrcp<float2> (pivoted QR of the recompression core)", "bound": "alu",
+                      "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk, "traffic": None,
+                      "launches_per_step": kern["KCORE_LAUNCHES"] / args.steps,
+                      "seconds_per_step": kern["KCORE_SECONDS"] / args.steps, "peak_source": src})
+    cands.sort(key=lambda c: -c["seconds_per_step"])
+    roof = dict(cands[0]) if cands else None
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 fill; c64 H-LU + f64 refinement" if prec == "fp32r" else "f64",
@@ -274,21 +317,26 @@ def main():
            "phases_s": per, "stats": stats, "gpu_launches": launches, "clocks": clocks,
            "e2e": {"value": N / e2e_s, "unit": "unknowns/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "wall_s": e2e_s},
-           "roofline": roof}
+           "roofline": roof, "kernels": cands[1:]}
     if not args.no_compare:
-        # the other precision on the same GPU: one untimed warm-up step, one step timed
-        other = "fp64" if prec == "fp32r" else "fp32r"
-        one_step(s, wl, dirs, precision=other)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        one_step(s, wl, dirs, precision=other)
-        e1.record(stream)
-        barrier()
-        cms = e0.elapsed_time(e1)
-        out["compare"] = {"precision": other, "value": N / (cms / 1000.0), "ms_per_step": cms, "steps": 1,
-                          "phases_s": {k: s.hm_query(k) for k in phases},
-                          "refine_iters": s.hm_query("REFINE_ITERS")}
+        # FP32 H-LU + FP64 refinement against the plain FP64 H-LU on the same GPU, one timed
+        # step each on a workload the FP64 path finishes in about a minute
+        cwl = load_workload(args.compare_workload)
+        cmp = {"workload": args.compare_workload}
+        for p in ("fp32r", "fp64"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            one_step(s, cwl, dirs, precision=p)
+            e1.record(stream)
+            barrier()
+            cms = e0.elapsed_time(e1)
+            cmp[p] = {"value": s.N / (cms / 1000.0), "unit": "unknowns/s", "ms_per_step": cms, "unknowns": s.N,
+                      "phases_s": {k: s.hm_query(k) for k in phases}, "refine_iters": s.hm_query("REFINE_ITERS"),
+                      "refine_res": s.hm_query("REFINE_RES")}
+        cmp["fp32r_speedup"] = cmp["fp64"]["ms_per_step"] / cmp["fp32r"]["ms_per_step"]
+        out["compare"] = cmp
+        progress("compare: %s" % json.dumps(cmp))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:

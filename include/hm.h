@@ -72,7 +72,7 @@ typedef struct {
     int aca_max_rank;     /* ACA rank bound before a block is split (0 = 160) */
     int precision;        /* hm_precision */
     int keep_matrix;      /* nonzero: keep an unfactored copy for hm_matvec after hm_factor */
-    double factor_tol;    /* HM_FP32_REFINED: truncation tolerance of the FP32 H-LU (0 = 1e-5) */
+    double factor_tol;    /* HM_FP32_REFINED: truncation tolerance of the FP32 H-LU (0 = 1e-4) */
     double refine_tol;    /* HM_FP32_REFINED: target relative residual per RHS (0 = 1e-10) */
     int refine_max_iter;  /* HM_FP32_REFINED: refinement step limit (0 = 30) */
 } hm_params;
@@ -124,7 +124,15 @@ enum {
     HM_Q_TRUNC_MAXK = 30,  /* largest number of columns K of one sum */
     HM_Q_TRUNC_WORK = 31,  /* sum of (m + n) K^2 over the sums */
     HM_Q_T_TRUNC = 32,     /* wall seconds spent in them (they synchronise) */
-    HM_Q_ACA_SKIPPED = 33  /* ACA attempts the rank model skipped (predicted rank >= 1.25 x bound) */
+    HM_Q_ACA_SKIPPED = 33, /* ACA attempts the rank model skipped (predicted rank >= 1.25 x bound) */
+    /* recompression kernels since the last hm_fill or hm_factor began, device time from
+     * CUDA events around each launch and algorithmic real flops: */
+    HM_Q_KQR_SECONDS = 34, /* Householder QR of the factors (one launch per batch) */
+    HM_Q_KQR_FLOPS = 35,
+    HM_Q_KQR_LAUNCHES = 36,
+    HM_Q_KCORE_SECONDS = 37,  /* core factorisation: pivoted QR (complex64) or Jacobi SVD (complex128) */
+    HM_Q_KCORE_FLOPS = 38,    /* counted for the pivoted QR only (the Jacobi sweep count varies) */
+    HM_Q_KCORE_LAUNCHES = 39
 };
 
 const char *hm_version(void);
@@ -192,7 +200,8 @@ const char *hm_last_error(hm_handle h);
  *
  * Features (HM_RANK_NFEAT = 8, float): log2|t|/10, log2|s|/10, diam(t)/(8 lambda),
  * diam(s)/(8 lambda), dist(t,s)/(8 lambda), max(diam)/dist/4, Nc/10, -log10(tol)/10,
- * with bounding-box diameters and distance (Eq. 21).  Target: log(1 + rank).
+ * with bounding-box diameters and distance (Eq. 21).  Target: log(1 + rank), with
+ * rank = twice the bound for an attempt that reached its bound (only a lower bound is known).
  *
  * Network: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = w3.h2 + b3 (FP32).
  * Packed parameters (host float[hm_mlp_num_params]): W1 [nh][nin] row-major, b1 [nh],

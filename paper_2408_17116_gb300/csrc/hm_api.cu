@@ -229,7 +229,7 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
         free_all(h);
         h->prm = *p;
         h->tol = p->aca_tol;
-        h->factor_tol = p->factor_tol > 0.0 ? p->factor_tol : 1e-5;
+        h->factor_tol = p->factor_tol > 0.0 ? p->factor_tol : 1e-4;
         if (h->prm.refine_tol <= 0.0) h->prm.refine_tol = 1e-10;
         if (h->prm.refine_max_iter <= 0) h->prm.refine_max_iter = 30;
         h->nc = nodes_per_dir;
@@ -272,6 +272,7 @@ hm_status hm_fill(hm_handle h)
         }
         const int nc = h->nc, w = 2 * nc * nc;
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
+        h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
         // near-field quadrature (A3)
         {
             Timer t(h->stream);
@@ -406,10 +407,10 @@ hm_status hm_fill(hm_handle h)
                     const bool hit = skipped || rf[nd + slot[i]] != 0;
                     const int rank_i = skipped ? 0 : rf[slot[i]];
                     if (!skipped && (!hit || sk[i] == sb[i])) {
-                        // training sample: the rank ACA needs (the bound when it was reached),
-                        // as log(1 + rank)
+                        // training sample, log(1 + rank): the rank ACA reached, or twice the bound
+                        // for a block that reached its bound (its rank is only known to exceed it)
                         h->rank_feat.insert(h->rank_feat.end(), &sf[HM_RANK_NFEAT * i], &sf[HM_RANK_NFEAT * (i + 1)]);
-                        h->rank_target.push_back((float)std::log(1.0 + (hit ? sb[i] : rank_i)));
+                        h->rank_target.push_back((float)std::log(1.0 + (hit ? 2.0 * sb[i] : rank_i)));
                         if (h->rank_model) {
                             pred_err += std::fabs((double)sp[i] - h->rank_target.back());
                             ++npred;
@@ -464,8 +465,11 @@ hm_status hm_fill(hm_handle h)
             rebuild_leaves(h);
             h->t_aca = t.stop();
         }
-        // QR + SVD recompression of every low-rank leaf (A6)
-        {
+        // QR + SVD recompression of every low-rank leaf (A6).  In HM_FP32_REFINED mode the
+        // FP64 H-matrix only serves the refinement residual: it keeps the ACA factors, and
+        // the complex64 copy is recompressed to factor_tol when hm_factor starts.
+        h->t_trunc = 0;
+        if (h->prm.precision != HM_FP32_REFINED) {
             Timer t(h->stream);
             std::vector<Block *> keep;
             std::vector<int> ranks;
@@ -499,6 +503,7 @@ hm_status hm_factor(hm_handle h)
         if (h->state != 2) throw HmError{HM_ERR_STATE, "hm_factor requires a filled, unfactored matrix"};
         h->flops_factor = 0;
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
+        h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
         if (h->prm.precision == HM_FP32_REFINED) {
             // the FP64 H-matrix stays unfactored: it is the refinement operator
             Timer t(h->stream);
@@ -743,6 +748,12 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_TRUNC_WORK: *out = h->tr_work; break;
         case HM_Q_T_TRUNC: *out = h->tr_seconds; break;
         case HM_Q_ACA_SKIPPED: *out = h->aca_skipped; break;
+        case HM_Q_KQR_SECONDS: *out = h->kqr_s; break;
+        case HM_Q_KQR_FLOPS: *out = h->kqr_flops; break;
+        case HM_Q_KQR_LAUNCHES: *out = h->kqr_n; break;
+        case HM_Q_KCORE_SECONDS: *out = h->kcore_s; break;
+        case HM_Q_KCORE_FLOPS: *out = h->kcore_flops; break;
+        case HM_Q_KCORE_LAUNCHES: *out = h->kcore_n; break;
         case HM_Q_REFINE_RES: *out = h->refine_res; break;
         case HM_Q_STORAGE32: {
             double w32 = 0;
@@ -789,6 +800,8 @@ void hm_destroy(hm_handle h)
     }
     cudaStreamSynchronize(h->stream);
     if (h->d_counter) cudaFree(h->d_counter);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 

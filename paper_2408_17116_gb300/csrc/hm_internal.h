@@ -128,6 +128,11 @@ struct hm_handle_s {
     double flops_factor = 0;
     // recompression statistics (reset by hm_fill and hm_factor)
     double tr_batches = 0, tr_jobs = 0, tr_maxk = 0, tr_work = 0, tr_seconds = 0;
+    // device time (CUDA events around each launch) and algorithmic real flops of the
+    // recompression kernels: Householder QR of the factors, and the core factorisation
+    // (pivoted QR for complex64, Jacobi SVD for complex128); reset with the statistics
+    double kqr_s = 0, kqr_flops = 0, kqr_n = 0, kcore_s = 0, kcore_flops = 0, kcore_n = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     long long launches = 0;
     int aca_nonconv = 0;
     unsigned long long near_points = 0;

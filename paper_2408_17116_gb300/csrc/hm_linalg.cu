@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 
 #include "hm_internal.h"
 
@@ -16,7 +17,7 @@
 // ---------------------------------------------------------------------------
 #define GB_M 64
 #define GB_N 64
-#define GB_K 8
+#define GB_K 16
 
 template <class C>
 struct GemmArgs {
@@ -46,6 +47,40 @@ __device__ __forceinline__ C loadB(const GemmArgs<C> &g, int p, int j)
     return g.opB ? zconj(g.B[(size_t)p * g.ldb + j]) : g.B[(size_t)j * g.ldb + p];
 }
 
+// Products of one staged k-slice into the NX x NY groups of 16 outputs a thread owns.
+// NX, NY are compile-time so a partial tile issues no products for padding (the
+// FP64 pipe of GB300 is the bound of the complex128 GEMMs).
+template <class C, int NX, int NY>
+__device__ __forceinline__ void gemm_slice(C (&acc)[4][4], const C (*As)[GB_M], const C (*Bs)[GB_N + 1], int tx,
+                                           int ty)
+{
+#pragma unroll
+    for (int pp = 0; pp < GB_K; ++pp) {
+        C a[NX], b[NY];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) a[q] = As[pp][tx + 16 * q];
+#pragma unroll
+        for (int q = 0; q < NY; ++q) b[q] = Bs[pp][ty + 16 * q];
+#pragma unroll
+        for (int x = 0; x < NX; ++x)
+#pragma unroll
+            for (int y = 0; y < NY; ++y) acc[x][y] = zfma(a[x], b[y], acc[x][y]);
+    }
+}
+
+template <class C, int NX>
+__device__ __forceinline__ void gemm_slice_nx(C (&acc)[4][4], const C (*As)[GB_M], const C (*Bs)[GB_N + 1], int tx,
+                                              int ty, int ny)
+{
+    switch (ny) {
+    case 1: gemm_slice<C, NX, 1>(acc, As, Bs, tx, ty); break;
+    case 2: gemm_slice<C, NX, 2>(acc, As, Bs, tx, ty); break;
+    case 3: gemm_slice<C, NX, 3>(acc, As, Bs, tx, ty); break;
+    case 4: gemm_slice<C, NX, 4>(acc, As, Bs, tx, ty); break;
+    default: break;  // no outputs in this warp
+    }
+}
+
 template <class C>
 __global__ void __launch_bounds__(256) k_zgemm(GemmArgs<C> g)
 {
@@ -60,19 +95,15 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs<C> g)
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = cmk<C>(0, 0);
-    // warp-uniform masks of the 16-row / 16-column groups that hold outputs: partial
-    // tiles skip the products of padding (on GB300 the FP64 pipe is the bound)
+    // 16-row groups holding outputs (uniform over the CTA) and 16-column groups holding
+    // outputs for this warp's threads (uniform over the warp)
     const int wy0 = j0 + ((tid >> 5) << 1);  // first column of this warp's threads
-    bool vx[4], vy[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        vx[q] = i0 + 16 * q < g.m;
-        vy[q] = wy0 + 16 * q < g.n;
-    }
+    const int nx = min(4, (g.m - i0 + 15) / 16);
+    const int ny = wy0 < g.n ? min(4, (g.n - wy0 + 15) / 16) : 0;
     for (int p0 = kb; p0 < ke; p0 += GB_K) {
-        // load 64 x 8 of A and 8 x 64 of B: 512 elements each, 2 per thread
+        // load 64 x GB_K of A and GB_K x 64 of B: 64 GB_K elements each, GB_K / 4 per thread
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < GB_K / 4; ++r) {
             int e = tid + r * 256;
             int ii = e & 63, pp = e >> 6;
             int gp = p0 + pp;
@@ -81,21 +112,11 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmArgs<C> g)
             Bs[pp][jj] = (gp < ke) ? loadB(g, gp, j0 + jj) : cmk<C>(0, 0);
         }
         __syncthreads();
-#pragma unroll
-        for (int pp = 0; pp < GB_K; ++pp) {
-            C a[4], b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[pp][tx + 16 * q];
-                b[q] = Bs[pp][ty + 16 * q];
-            }
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                if (!vx[x]) continue;
-#pragma unroll
-                for (int y = 0; y < 4; ++y)
-                    if (vy[y]) acc[x][y] = zfma(a[x], b[y], acc[x][y]);
-            }
+        switch (nx) {
+        case 1: gemm_slice_nx<C, 1>(acc, As, Bs, tx, ty, ny); break;
+        case 2: gemm_slice_nx<C, 2>(acc, As, Bs, tx, ty, ny); break;
+        case 3: gemm_slice_nx<C, 3>(acc, As, Bs, tx, ty, ny); break;
+        default: gemm_slice_nx<C, 4>(acc, As, Bs, tx, ty, ny); break;
         }
         __syncthreads();
     }
@@ -580,6 +601,17 @@ struct SVDDesc {
     int *ord;
 };
 
+// Real flops of a complex Householder QR of an M x K matrix, r = min(M, K) reflectors,
+// with the explicit M x r Q: each reflector j updates the (M - j) x (K - j - 1) trailing
+// block (8 real flops per complex multiply-add, two passes) and later the (M - j) x (r - j)
+// block of Q.
+static double householder_flops(int M, int K, int r)
+{
+    double f = 0;
+    for (int j = 0; j < r; ++j) f += 16.0 * (M - j) * ((K - j - 1) + (r - j));
+    return f;
+}
+
 // Relative size of an off-diagonal inner product below which a Jacobi rotation is skipped.
 template <class R> __device__ __forceinline__ R jacobi_eps();
 template <> __device__ __forceinline__ double jacobi_eps<double>() { return 1e-14; }
@@ -697,6 +729,195 @@ __global__ void k_gather_cols(const C *M, int p, const int *ord, const typename 
 }
 
 // ---------------------------------------------------------------------------
+// Column-pivoted Householder QR of the core, stopped at the Frobenius tolerance
+// (the complex64 factor's truncation), one CTA per core M (p x q, ld p):
+//   M Pi = Q R;  stop at the first j with sum_{l >= j} |trailing column l|^2 <= tol2 |M|_F^2,
+// so |M - Q[:, :k] R[:k, :] Pi^T|_F <= tol |M|_F with k the returned rank.
+// Outputs: Qc (p x k) explicit, W (q x k) = (R[:k, :] Pi^T)^H, *rank = k.
+// Scratch (global): cn [q] column norms, perm [q], beta [min(p, q)], diag [min(p, q)].
+// ---------------------------------------------------------------------------
+template <class C>
+struct QRCPDesc {
+    C *M;
+    int p, q;
+    C *Qc, *W;
+    typename CReal<C>::R *cn, *beta, *diag_re, *diag_im;
+    int *perm;
+    int *rank;
+};
+
+template <class R>
+__device__ R qrcp_sum(R v, R *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffff, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R s = 0;
+        for (int w = 0; w < QR_T / 32; ++w) s += sh[w];
+        sh[32] = s;
+    }
+    __syncthreads();
+    R r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+template <class C>
+__global__ void __launch_bounds__(QR_T) k_qrcp(const QRCPDesc<C> *__restrict__ descs, double tol2)
+{
+    typedef typename CReal<C>::R R;
+    const QRCPDesc<C> d = descs[blockIdx.x];
+    const int p = d.p, q = d.q, r = min(p, q);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_T / 32;
+    __shared__ R sh[33];
+    __shared__ R shv[QR_T / 32];
+    __shared__ int shi[QR_T / 32];
+    __shared__ int s_piv;
+    C *M = d.M;
+    // column norms and the identity permutation
+    for (int l = warp; l < q; l += nw) {
+        R s = 0;
+        for (int i = lane; i < p; i += 32) s += zabs2(M[(size_t)l * p + i]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
+        if (lane == 0) {
+            d.cn[l] = s;
+            d.perm[l] = l;
+        }
+    }
+    __syncthreads();
+    R part = 0;
+    for (int l = tid; l < q; l += QR_T) part += d.cn[l];
+    const R total = qrcp_sum(part, sh);
+    int k = 0;
+    for (int j = 0; j < r; ++j) {
+        // remaining squared Frobenius norm and the pivot column (largest, ties to lowest)
+        R rem = 0, bv = -1;
+        int bi = 0x7fffffff;
+        for (int l = j + tid; l < q; l += QR_T) {
+            R c = d.cn[l];
+            rem += c;
+            if (c > bv) {
+                bv = c;
+                bi = l;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            R v2 = __shfl_down_sync(0xffffffff, bv, o);
+            int i2 = __shfl_down_sync(0xffffffff, bi, o);
+            if (v2 > bv || (v2 == bv && i2 < bi)) {
+                bv = v2;
+                bi = i2;
+            }
+        }
+        if (lane == 0) {
+            shv[warp] = bv;
+            shi[warp] = bi;
+        }
+        rem = qrcp_sum(rem, sh);  // contains the barriers that publish shv / shi
+        if (tid == 0) {
+            R v = shv[0];
+            int ii = shi[0];
+            for (int w = 1; w < nw; ++w)
+                if (shv[w] > v || (shv[w] == v && shi[w] < ii)) {
+                    v = shv[w];
+                    ii = shi[w];
+                }
+            s_piv = ii;
+        }
+        __syncthreads();
+        if (!(rem > (R)tol2 * total)) break;
+        const int pv = s_piv;
+        if (pv != j) {
+            for (int i = tid; i < p; i += QR_T) {
+                C t = M[(size_t)j * p + i];
+                M[(size_t)j * p + i] = M[(size_t)pv * p + i];
+                M[(size_t)pv * p + i] = t;
+            }
+            if (tid == 0) {
+                R t = d.cn[j];
+                d.cn[j] = d.cn[pv];
+                d.cn[pv] = t;
+                int tp = d.perm[j];
+                d.perm[j] = d.perm[pv];
+                d.perm[pv] = tp;
+            }
+            __syncthreads();
+        }
+        // Householder reflector of M[j:, j]
+        C *x = M + (size_t)j * p;
+        R nrm2 = 0;
+        for (int i = j + tid; i < p; i += QR_T) nrm2 += zabs2(x[i]);
+        nrm2 = qrcp_sum(nrm2, sh);
+        if (tid == 0) {
+            R nrm = sqrt(nrm2);
+            C x0 = x[j];
+            R a0 = sqrt(zabs2(x0));
+            C ph = a0 > 0 ? zscale(x0, (R)1 / a0) : cmk<C>(1, 0);
+            C alpha = zscale(ph, -nrm);
+            x[j] = zsub(x0, alpha);
+            R vhv = 2 * (nrm2 + nrm * a0);
+            d.beta[j] = vhv > 0 ? 2 / vhv : 0;
+            d.diag_re[j] = alpha.x;
+            d.diag_im[j] = alpha.y;
+        }
+        __syncthreads();
+        const R beta = d.beta[j];
+        // apply to the trailing columns and recompute their norms below row j
+        for (int l = j + 1 + warp; l < q; l += nw) {
+            C *a = M + (size_t)l * p;
+            C s = cmk<C>(0, 0);
+            for (int i = j + lane; i < p; i += 32) s = zfmac(x[i], a[i], s);
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffff, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffff, s.y, o);
+            }
+            s = zscale(s, beta);
+            R nn = 0;
+            for (int i = j + lane; i < p; i += 32) {
+                C v = zsub(a[i], zmul(x[i], s));
+                a[i] = v;
+                if (i > j) nn += zabs2(v);
+            }
+            for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffff, nn, o);
+            if (lane == 0) d.cn[l] = nn;
+        }
+        __syncthreads();
+        k = j + 1;
+    }
+    if (tid == 0) *d.rank = k;
+    if (k == 0) return;
+    // W (q x k): W[perm[l], t] = conj(R[t, l]),  R[t, l] = M[t, l] (t < l), alpha_t (t = l), 0 (t > l)
+    for (int e = tid; e < q * k; e += QR_T) {
+        const int l = e % q, t = e / q;
+        C v = t < l ? M[(size_t)l * p + t] : (t == l ? cmk<C>(d.diag_re[t], d.diag_im[t]) : cmk<C>(0, 0));
+        d.W[(size_t)t * q + d.perm[l]] = zconj(v);
+    }
+    // Qc (p x k) = H_0 ... H_{k-1} [I_k; 0]
+    for (int e = tid; e < p * k; e += QR_T) {
+        const int i = e % p, c = e / p;
+        d.Qc[(size_t)c * p + i] = cmk<C>(i == c ? 1 : 0, 0);
+    }
+    __syncthreads();
+    for (int j = k - 1; j >= 0; --j) {
+        const C *v = M + (size_t)j * p;
+        const R beta = d.beta[j];
+        for (int c = j + warp; c < k; c += nw) {
+            C *qc = d.Qc + (size_t)c * p;
+            C s = cmk<C>(0, 0);
+            for (int i = j + lane; i < p; i += 32) s = zfmac(v[i], qc[i], s);
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffff, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffff, s.y, o);
+            }
+            s = zscale(s, beta);
+            for (int i = j + lane; i < p; i += 32) qc[i] = zsub(qc[i], zmul(v[i], s));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Truncated recompression of U V^H (batched): QR of both factors, SVD of the core
 // R_U R_V^H, keep the smallest rank k' with sqrt(sum_{i>k'} s_i^2) <= tol |s|_2.
 // ---------------------------------------------------------------------------
@@ -720,6 +941,7 @@ template <class C>
 static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
 {
     typedef typename CReal<C>::R R;
+    const bool qrcp = std::is_same<C, cf>::value;
     // workspace and copies
     std::vector<QRDesc<C>> qd;
     for (auto &J : jobs) {
@@ -732,11 +954,11 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
         J.RU = (C *)dalloc(h, sizeof(C) * (size_t)J.r1 * J.K);
         J.RV = (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * J.K);
         J.Mc = (C *)dalloc(h, sizeof(C) * (size_t)J.r1 * J.r2);
-        J.Y = (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * J.r2);
-        J.bU = (R *)dalloc(h, sizeof(R) * (J.r1 + J.r2 + J.r2));
+        J.Y = qrcp ? nullptr : (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * J.r2);
+        J.bU = (R *)dalloc(h, sizeof(R) * (J.r1 + 3 * J.r2));
         J.bV = J.bU + J.r1;
         J.S = J.bV + J.r2;
-        J.ord = (int *)dalloc(h, sizeof(int) * J.r2);
+        J.ord = (int *)dalloc(h, sizeof(int) * (J.r2 + 1));
         zcopy2d(h, MVT<C>{J.Ua, J.m, J.K, J.m}, MVT<C>{(C *)J.U, J.m, J.K, J.ldu});
         zcopy2d(h, MVT<C>{J.Va, J.n, J.K, J.n}, MVT<C>{(C *)J.V, J.n, J.K, J.ldv});
         qd.push_back(QRDesc<C>{J.Ua, J.m, J.K, J.QU, J.RU, J.bU});
@@ -745,25 +967,82 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
     }
     QRDesc<C> *d_qd = (QRDesc<C> *)dalloc(h, sizeof(QRDesc<C>) * qd.size());
     HM_CUDA(cudaMemcpyAsync(d_qd, qd.data(), sizeof(QRDesc<C>) * qd.size(), cudaMemcpyHostToDevice, h->stream));
+    for (int e = 0; e < 4; ++e)
+        if (!h->ev[e]) HM_CUDA(cudaEventCreate(&h->ev[e]));
+    HM_CUDA(cudaEventRecord(h->ev[0], h->stream));
     k_qr<C><<<(unsigned)qd.size(), QR_T, 0, h->stream>>>(d_qd);
     HM_CHECK_LAUNCH();
+    HM_CUDA(cudaEventRecord(h->ev[1], h->stream));
     count_launch(h);
+    for (auto &J : jobs) h->kqr_flops += householder_flops(J.m, J.K, J.r1) + householder_flops(J.n, J.K, J.r2);
     // core M = R_U R_V^H
     for (auto &J : jobs)
         zgemm<C>(h, 'N', 'C', J.r1, J.r2, J.K, cmk<C>(1, 0), J.RU, J.r1, J.RV, J.r2, cmk<C>(0, 0), J.Mc, J.r1);
-    std::vector<SVDDesc<C>> sd;
-    for (auto &J : jobs) sd.push_back(SVDDesc<C>{J.Mc, J.r1, J.r2, J.Y, J.S, J.ord});
-    int qmax = 0;
-    for (auto &J : jobs) qmax = std::max(qmax, J.r2);
-    if (qmax > SVD_QMAX) throw HmError{HM_ERR_NUMERIC, "recompression core too large: " + std::to_string(qmax)};
-    SVDDesc<C> *d_sd = (SVDDesc<C> *)dalloc(h, sizeof(SVDDesc<C>) * sd.size());
-    HM_CUDA(cudaMemcpyAsync(d_sd, sd.data(), sizeof(SVDDesc<C>) * sd.size(), cudaMemcpyHostToDevice, h->stream));
-    k_svd<C><<<(unsigned)sd.size(), SVD_T, 0, h->stream>>>(d_sd);
+    void *d_desc = nullptr;
+    if (qrcp) {
+        // complex64 factor: column-pivoted QR of the core, stopped at the tolerance;
+        // Qc -> RU, W -> RV (both large enough), scratch in bU/bV/S, perm and rank in ord
+        std::vector<QRCPDesc<C>> cd;
+        for (auto &J : jobs)
+            cd.push_back(QRCPDesc<C>{J.Mc, J.r1, J.r2, J.RU, J.RV, J.S, J.bU, J.bV, J.S + J.r2, J.ord,
+                                     J.ord + J.r2});
+        d_desc = dalloc(h, sizeof(QRCPDesc<C>) * cd.size());
+        HM_CUDA(cudaMemcpyAsync(d_desc, cd.data(), sizeof(QRCPDesc<C>) * cd.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+        HM_CUDA(cudaEventRecord(h->ev[2], h->stream));
+        k_qrcp<C><<<(unsigned)cd.size(), QR_T, 0, h->stream>>>((const QRCPDesc<C> *)d_desc, h->cur_tol * h->cur_tol);
+    } else {
+        std::vector<SVDDesc<C>> sd;
+        for (auto &J : jobs) sd.push_back(SVDDesc<C>{J.Mc, J.r1, J.r2, J.Y, J.S, J.ord});
+        int qmax = 0;
+        for (auto &J : jobs) qmax = std::max(qmax, J.r2);
+        if (qmax > SVD_QMAX) throw HmError{HM_ERR_NUMERIC, "recompression core too large: " + std::to_string(qmax)};
+        d_desc = dalloc(h, sizeof(SVDDesc<C>) * sd.size());
+        HM_CUDA(cudaMemcpyAsync(d_desc, sd.data(), sizeof(SVDDesc<C>) * sd.size(), cudaMemcpyHostToDevice, h->stream));
+        HM_CUDA(cudaEventRecord(h->ev[2], h->stream));
+        k_svd<C><<<(unsigned)sd.size(), SVD_T, 0, h->stream>>>((const SVDDesc<C> *)d_desc);
+    }
     HM_CHECK_LAUNCH();
+    HM_CUDA(cudaEventRecord(h->ev[3], h->stream));
     count_launch(h);
-    HM_CUDA(cudaStreamSynchronize(h->stream));
     dfree(h, d_qd);
-    dfree(h, d_sd);
+    dfree(h, d_desc);  // stream-ordered: released after the kernel
+}
+
+// QRCP variant of stage 2: U' = Q_U Qc, V' = Q_V W with the rank the kernel chose.
+template <class C>
+static int trunc_stage2_qrcp(hm_handle_s *h, TruncJob<C> &J, int kk, C **Uo, C **Vo)
+{
+    *Uo = nullptr;
+    *Vo = nullptr;
+    if (kk > 0) {
+        *Uo = (C *)dalloc(h, sizeof(C) * (size_t)J.m * kk);
+        *Vo = (C *)dalloc(h, sizeof(C) * (size_t)J.n * kk);
+        zgemm<C>(h, 'N', 'N', J.m, kk, J.r1, cmk<C>(1, 0), J.QU, J.m, J.RU, J.r1, cmk<C>(0, 0), *Uo, J.m);
+        zgemm<C>(h, 'N', 'N', J.n, kk, J.r2, cmk<C>(1, 0), J.QV, J.n, J.RV, J.r2, cmk<C>(0, 0), *Vo, J.n);
+    }
+    dfree(h, J.Ua);
+    dfree(h, J.Va);
+    dfree(h, J.QU);
+    dfree(h, J.QV);
+    dfree(h, J.RU);
+    dfree(h, J.RV);
+    dfree(h, J.Mc);
+    dfree(h, J.bU);
+    dfree(h, J.ord);
+    return kk;
+}
+
+// After the batch's synchronisation: accumulate the device times of its two kernels.
+static void account_kernels(hm_handle_s *h)
+{
+    float a = 0, b = 0;
+    HM_CUDA(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+    HM_CUDA(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
+    h->kqr_s += 1e-3 * a;
+    h->kqr_n += 1;
+    h->kcore_s += 1e-3 * b;
+    h->kcore_n += 1;
 }
 
 // returns the kept rank; allocates *Uo (m x k'), *Vo (n x k')
@@ -821,6 +1100,15 @@ static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector
     typedef typename CReal<C>::R R;
     S.resize(jobs.size());
     ord.resize(jobs.size());
+    if (std::is_same<C, cf>::value) {
+        // QRCP: only the chosen ranks come back (ord[i][0])
+        std::vector<int> rk(jobs.size());
+        for (size_t i = 0; i < jobs.size(); ++i)
+            HM_CUDA(cudaMemcpyAsync(&rk[i], jobs[i].ord + jobs[i].r2, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        for (size_t i = 0; i < jobs.size(); ++i) ord[i].assign(1, rk[i]);
+        return;
+    }
     std::vector<std::vector<R>> Sr(jobs.size());
     for (size_t i = 0; i < jobs.size(); ++i) {
         Sr[i].resize(jobs[i].r2);
@@ -848,10 +1136,16 @@ int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const 
     jobs[0].V = V;
     jobs[0].ldv = ldv;
     jobs[0].kmax = kmax;
+    double saved = h->cur_tol;
+    h->cur_tol = tol;
     trunc_stage1(h, jobs);
+    h->cur_tol = saved;
     std::vector<std::vector<double>> S;
     std::vector<std::vector<int>> ord;
     fetch_sv(h, jobs, S, ord);
+    account_kernels(h);
+    if (std::is_same<C, cf>::value) h->kcore_flops += householder_flops(jobs[0].r1, jobs[0].r2, ord[0][0]);
+    if (std::is_same<C, cf>::value) return trunc_stage2_qrcp(h, jobs[0], std::min(ord[0][0], kmax > 0 ? kmax : K), Uo, Vo);
     return trunc_stage2(h, jobs[0], S[0], ord[0], tol, Uo, Vo);
 }
 
@@ -888,14 +1182,21 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
             h->tr_maxk = std::max(h->tr_maxk, (double)J.K);
             h->tr_work += ((double)J.m + J.n) * J.K * J.K;
         }
+        double saved = h->cur_tol;
+        h->cur_tol = tol;
         trunc_stage1(h, jobs);
+        h->cur_tol = saved;
         std::vector<std::vector<double>> S;
         std::vector<std::vector<int>> ord;
         fetch_sv(h, jobs, S, ord);
+        account_kernels(h);
+        if (std::is_same<C, cf>::value)
+            for (size_t t = 0; t < jobs.size(); ++t) h->kcore_flops += householder_flops(jobs[t].r1, jobs[t].r2, ord[t][0]);
         for (size_t t = 0; t < jobs.size(); ++t) {
             BlockT<C> *b = blks[idx[t]];
             C *Uo, *Vo;
-            int kk = trunc_stage2(h, jobs[t], S[t], ord[t], tol, &Uo, &Vo);
+            int kk = std::is_same<C, cf>::value ? trunc_stage2_qrcp(h, jobs[t], ord[t][0], &Uo, &Vo)
+                                                : trunc_stage2(h, jobs[t], S[t], ord[t], tol, &Uo, &Vo);
             dfree(h, b->U);
             dfree(h, b->V);
             b->U = Uo;

@@ -57,6 +57,10 @@ def workload(name):
         kh, pol = incidence(4)
         return dict(name=name, bodies=body(semi=(4.0,) * 3)[None], ms=[4], nc=10, k=K0,
                     leaf=128, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol, radius=4.0)
+    if name == "sphere_d4_m2_nc10":  # PEC sphere, 4 wavelengths, 4,800 unknowns (precision comparison)
+        kh, pol = incidence(4)
+        return dict(name=name, bodies=body(semi=(2.0,) * 3)[None], ms=[2], nc=10, k=K0,
+                    leaf=128, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol, radius=2.0)
     if name == "sphere_d2_m2_nc6":  # mid-size parity case: 1,728 unknowns, ragged leaves
         kh, pol = incidence(2, SEED + 1)
         return dict(name=name, bodies=body(semi=(1.0,) * 3)[None], ms=[2], nc=6, k=K0,
@@ -70,7 +74,7 @@ def workload(name):
     raise KeyError(name)
 
 
-WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d2_m2_nc6", "ellipsoid_small")
+WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d4_m2_nc10", "sphere_d2_m2_nc6", "ellipsoid_small")
 
 
 def mlp_init(nin, nh, seed=SEED):
