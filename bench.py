@@ -163,6 +163,22 @@ def wl_N(wl):
 PRECISION = {"fp32r": 1, "fp64": 0}
 
 
+def aggregate(ms_local, unknowns_local, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: the slowest rank's time per step (max over ranks)
+    and the unknowns all ranks solved per second.  Returns (ms_max, unknowns_per_s)."""
+    import torch
+    world = dist.get_world_size() if dist is not None else 1
+    t = torch.tensor([float(ms_local), float(unknowns_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tn = t[1:].clone()
+        dist.all_reduce(tn, op=dist.ReduceOp.SUM)
+        t = torch.cat([tm, tn])
+    ms = float(t[0].item())
+    return ms, float(t[1].item()) / (ms / 1000.0) if world else 0.0
+
+
 def one_step(s, wl, dirs, host=False, precision="fp32r"):
     s.hm_build_geometry(wl["bodies"], wl["ms"], wl["nc"], wl["k"], wl["leaf"], wl["eta"], wl["aca_tol"],
                         precision=PRECISION[precision])
@@ -256,12 +272,8 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     progress("timed: %.1f ms per step" % ms)
     launches = int(s.hm_query("LAUNCHES") - L0)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     N = s.N
-    value = N * world / (ms / 1000.0)
+    ms, value = aggregate(ms, N, dist, device="cuda")
     stats = {k.lower(): s.hm_query(k) for k in ("CR", "MAX_RANK", "MEAN_RANK", "LR_BLOCKS", "DENSE_BLOCKS",
                                                  "NEAR_PAIRS", "ACA_NONCONV", "FLOPS_FACTOR", "REFINE_ITERS",
                                                  "REFINE_RES", "STORAGE", "STORAGE32")}
