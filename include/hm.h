@@ -181,6 +181,23 @@ hm_status hm_solve_host(hm_handle h, int nrhs, const double *inc_dirs, const dou
 hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const double *obs_dirs,
                       void *efar_dev, double *rcs_host);
 
+/* hm_farfield without device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let the library allocate device memory during
+ * a call (their device memory belongs to their own pool or allocator, or their loop
+ * forbids allocation after start-up).  Same arguments, results and synchronisation
+ * as hm_farfield, but the observation directions and the RCS values are staged in one
+ * static device array of HM_FARFIELD_STATIC_DOUBLES doubles (512 KiB, held by every
+ * GPU that loads the library until the process exits) instead of buffers allocated
+ * per call.  Limit: 3 nang + nrhs nang (nrhs nang only when rcs_host is given) must
+ * not exceed HM_FARFIELD_STATIC_DOUBLES, otherwise HM_ERR_ARG and nothing runs.
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  All
+ * calls share the array, which keeps the last call's contents: calls that overlap on
+ * the GPU (other streams or other host threads) race on it. */
+#define HM_FARFIELD_STATIC_DOUBLES 65536
+hm_status hm_farfield_static(hm_handle h, int nrhs, const void *x_dev, int nang, const double *obs_dirs,
+                             void *efar_dev, double *rcs_host);
+
 /* y_dev = A x_dev for nrhs vectors [nrhs][N] (natural order) with the FP64 H-matrix
  * (available after hm_fill; after hm_factor only with keep_matrix). */
 hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev);

@@ -30,7 +30,8 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_get_nodes_host", "hm_get_near_pairs_host", "hm_get_near_block_host", "hm_entries_host",
            "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host", "hm_rank_samples",
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
-           "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy")
+           "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
+           "hm_farfield_static")
 
 
 class hm_params(ctypes.Structure):
@@ -74,6 +75,7 @@ def load(path=SO):
     L.hm_solve_host.argtypes = [P, I, P, P, P]
     L.hm_farfield.argtypes = [P, I, P, I, P, P, P]
     L.hm_matvec.argtypes = [P, I, P, P]
+    L.hm_farfield_static.argtypes = [P, I, P, I, P, P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
@@ -192,6 +194,18 @@ class Solver:
         rcs = np.empty((nrhs, d.shape[0]))
         self._check(self.L.hm_farfield(self.h, nrhs, ctypes.c_void_p(x.data_ptr()), d.shape[0], _np_ptr(d),
                                        ctypes.c_void_p(efar.data_ptr() if efar is not None else 0), _np_ptr(rcs)))
+        return efar, rcs
+
+    def hm_farfield_static(self, x, dirs, want_efar=True):
+        """hm_farfield through the entry point that allocates no device memory."""
+        d = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
+        x = x.reshape(-1, self.N)
+        nrhs = x.shape[0]
+        efar = self.torch.empty((nrhs, d.shape[0], 3), dtype=self.torch.complex128, device="cuda") if want_efar else None
+        rcs = np.empty((nrhs, d.shape[0]))
+        self._check(self.L.hm_farfield_static(self.h, nrhs, ctypes.c_void_p(x.data_ptr()), d.shape[0], _np_ptr(d),
+                                              ctypes.c_void_p(efar.data_ptr() if efar is not None else 0),
+                                              _np_ptr(rcs)))
         return efar, rcs
 
     def hm_matvec(self, x):
