@@ -200,24 +200,6 @@ def test_error_codes_and_call_order():
     assert e.value.status == 1
 
 
-def test_mid_size_fp64_sampled_residual():
-    # the plain FP64 H-LU on the 4-wavelength sphere (4,800 unknowns): residual of sampled
-    # rows of the oracle matrix (the 19,200-unknown case runs in FP32 + refinement below)
-    wl = workloads.workload("sphere_d4_m2_nc10")
-    s = make_solver(wl)
-    s.hm_fill()
-    s.hm_factor()
-    x = s.hm_solve(wl["kdirs"], wl["pols"]).cpu().numpy()
-    o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
-    b = o.rhs(wl["kdirs"], wl["pols"])
-    rng = np.random.default_rng(11)
-    rows = rng.choice(o.N, 48, replace=False)
-    R = o.matrix_rows(rows)
-    for r in range(x.shape[0]):
-        res = R @ x[r] - b[r][rows]
-        assert np.linalg.norm(res) / np.linalg.norm(b[r][rows]) <= 1e-5
-
-
 @pytest.mark.parametrize("name", SMALL)
 def test_fp32_factor_with_fp64_refinement_against_dense_oracle(name):
     # FP32 H-LU as a preconditioner, FP64 refinement against the FP64 H-matrix
