@@ -41,3 +41,39 @@ def test_create_without_gpu_reports_an_error_or_succeeds():
         lib.hm_destroy(h)
     else:
         assert st in (3, 4)
+
+
+def _header_enum(prefix):
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "hm.h")).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(%s\w+)\s*=\s*(\d+)" % prefix, src)}
+
+
+def test_binding_constants_match_the_header():
+    q = _header_enum("HM_Q_")
+    assert q and {k[len("HM_Q_"):]: v for k, v in q.items()} == hm.Q
+    st = _header_enum("HM_ERR_")
+    st["HM_OK"] = 0
+    assert {v: k for k, v in st.items()} == hm.STATUS
+    prec = _header_enum("HM_FP")
+    assert prec == {"HM_FP64": hm.HM_FP64, "HM_FP32_REFINED": hm.HM_FP32_REFINED}
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    # sizes and offsets of the ABI structs as the C compiler lays them out
+    fields = {"hm_params": [f for f, _ in hm.hm_params._fields_], "hm_body": [f for f, _ in hm.hm_body._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hm.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st, st))
+        for f in fs:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st, f, st, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)], text=True).split("\n") if line)
+    for st, cls in (("hm_params", hm.hm_params), ("hm_body", hm.hm_body)):
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert int(out["%s.%s" % (st, f)]) == getattr(cls, f).offset, (st, f)
