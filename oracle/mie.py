@@ -1,4 +1,4 @@
-"""Mie series for a PEC sphere -- TEST INFRASTRUCTURE ONLY.
+"""Mie series for PEC and dielectric spheres -- TEST INFRASTRUCTURE ONLY.
 
 The closed-form anchor the paper itself validates against (Sec. IV.A, Table 1:
 density errors against the analytical Mie series).  Written from the textbook
@@ -168,3 +168,112 @@ def pec_surface_current(k, radius, theta, phi, eta):
     th_hat = np.array([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)])
     ph_hat = np.array([-np.sin(phi), np.cos(phi), 0.0])
     return np.conj(Jth * th_hat + Jph * ph_hat)
+
+
+# ---------------------------------------------------------------------------
+# Dielectric (penetrable, non-magnetic) sphere: the closed form the paper's
+# dielectric results are checked against (Sec. IV.B).  Bohren & Huffman, Ch. 4,
+# exp(-i w t) convention, relative refractive index m = sqrt(eps_r) of the sphere
+# to its surroundings, mu = 1 on both sides.
+# ---------------------------------------------------------------------------
+
+def log_derivative(nmax, z):
+    """D_n(z) = psi_n'(z) / psi_n(z), n = 0..nmax, by the downward recurrence
+    D_{n-1} = n/z - 1/(D_n + n/z) started from zero far above max(nmax, |z|)
+    (stable for large |z|, Wiscombe 1980).  z may be complex."""
+    z = complex(z)
+    nst = int(max(nmax, abs(z)) + 16 + 4.0 * abs(z) ** (1.0 / 3.0))
+    D = np.zeros(nst + 1, dtype=complex)
+    for n in range(nst, 0, -1):
+        D[n - 1] = n / z - 1.0 / (D[n] + n / z)
+    return D[: nmax + 1]
+
+
+def dielectric_coefficients(x, m, nmax=None):
+    """Scattering coefficients a_n, b_n, n = 1..nmax, of a sphere of size x = k a and
+    relative index m, written with the logarithmic derivative of psi_n(m x):
+      a_n = [(D_n/m + n/x) psi_n - psi_{n-1}] / [(D_n/m + n/x) xi_n - xi_{n-1}]
+      b_n = [(m D_n + n/x) psi_n - psi_{n-1}] / [(m D_n + n/x) xi_n - xi_{n-1}]."""
+    if nmax is None:
+        nmax = nmax_for(x)
+    psi, dpsi, xi, dxi, _, _ = riccati(nmax, x)
+    D = log_derivative(nmax, m * x)[1:]
+    n = np.arange(1, nmax + 1)
+    ta = D / m + n / x
+    tb = m * D + n / x
+    a = (ta * psi[1:] - psi[:-1]) / (ta * xi[1:] - xi[:-1])
+    b = (tb * psi[1:] - psi[:-1]) / (tb * xi[1:] - xi[:-1])
+    return a, b
+
+
+def dielectric_interior_coefficients(x, m, nmax=None):
+    """Interior coefficients c_n, d_n (real m, mu = 1) from the same boundary conditions:
+      c_n = (j_n(x) [x h_n(x)]' - h_n(x) [x j_n(x)]') / (j_n(mx) [x h_n(x)]' - h_n(x) [mx j_n(mx)]')
+      d_n = m (j_n(x) [x h_n(x)]' - h_n(x) [x j_n(x)]') / (m^2 j_n(mx) [x h_n(x)]' - h_n(x) [mx j_n(mx)]')."""
+    if nmax is None:
+        nmax = nmax_for(x)
+    _, dpsi, _, dxi, jn, h = riccati(nmax, x)
+    _, dpsim, _, _, jnm, _ = riccati(nmax, m * x)
+    num = jn[1:] * dxi[1:] - h[1:] * dpsi[1:]
+    c = num / (jnm[1:] * dxi[1:] - h[1:] * dpsim[1:])
+    d = m * num / (m * m * jnm[1:] * dxi[1:] - h[1:] * dpsim[1:])
+    return c, d
+
+
+def dielectric_fields_bh(k, radius, m, r, theta, phi, eta=1.0, part="total"):
+    """E and H (spherical components, exp(-i w t)) for incident E = x exp(ikz): outside
+    (r >= radius: incident + scattered) or inside (r <= radius, part = "interior")."""
+    x = k * radius
+    nmax = nmax_for(max(x, k * r))
+    n = np.arange(1, nmax + 1)
+    En = (1j ** n) * (2 * n + 1) / (n * (n + 1))
+    if part == "interior":
+        c, d = dielectric_interior_coefficients(x, m, nmax)
+        M1e, M1o, N1e, N1o = _vsh(n, m * k * r, theta, phi, 1)
+        E = np.sum(En * (c * M1o - 1j * d * N1e), axis=1)
+        H = -(m / eta) * np.sum(En * (d * M1e + 1j * c * N1o), axis=1)
+        return E, H
+    a, b = dielectric_coefficients(x, m, nmax)
+    rho = k * r
+    M1e, M1o, N1e, N1o = _vsh(n, rho, theta, phi, 1)
+    M3e, M3o, N3e, N3o = _vsh(n, rho, theta, phi, 3)
+    Ei = np.sum(En * (M1o - 1j * N1e), axis=1)
+    Hi = -np.sum(En * (M1e + 1j * N1o), axis=1) / eta
+    Es = np.sum(En * (1j * a * N3e - b * M3o), axis=1)
+    Hs = np.sum(En * (1j * b * N3o + a * M3e), axis=1) / eta
+    if part == "scattered":
+        return Es, Hs
+    return Ei + Es, Hi + Hs
+
+
+def dielectric_surface_currents(k, radius, m, theta, phi, eta):
+    """J = n x H and M = E x n on the outer side of r = radius, Cartesian vectors in the
+    exp(j w t) convention (conjugates of the exp(-i w t) phasors)."""
+    E, H = dielectric_fields_bh(k, radius, m, radius, theta, phi, eta=eta)
+    th_hat = np.array([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)])
+    ph_hat = np.array([-np.sin(phi), np.cos(phi), 0.0])
+    J = -H[2] * th_hat + H[1] * ph_hat       # r x (H_th th + H_ph ph)
+    M = E[2] * th_hat - E[1] * ph_hat        # (E_th th + E_ph ph) x r
+    return np.conj(J), np.conj(M)
+
+
+def dielectric_rcs(k, radius, m, theta, phi):
+    """Bistatic RCS (m^2), incidence along +z, x-polarised, unit amplitude."""
+    x = k * radius
+    a, b = dielectric_coefficients(x, m)
+    nmax = a.size
+    pi, tau = pi_tau(nmax, np.cos(theta))
+    n = np.arange(1, nmax + 1)
+    c = ((2 * n + 1) / (n * (n + 1)))[:, None]
+    S1 = np.sum(c * (a[:, None] * pi + b[:, None] * tau), axis=0)
+    S2 = np.sum(c * (a[:, None] * tau + b[:, None] * pi), axis=0)
+    return 4 * np.pi / k ** 2 * (np.abs(S2) ** 2 * np.cos(phi) ** 2 + np.abs(S1) ** 2 * np.sin(phi) ** 2)
+
+
+def dielectric_cross_sections(k, radius, m):
+    x = k * radius
+    a, b = dielectric_coefficients(x, m)
+    n = np.arange(1, a.size + 1)
+    sca = 2 * np.pi / k ** 2 * np.sum((2 * n + 1) * (np.abs(a) ** 2 + np.abs(b) ** 2))
+    ext = 2 * np.pi / k ** 2 * np.sum((2 * n + 1) * np.real(a + b))
+    return sca, ext
