@@ -2,7 +2,9 @@
 
 Plain, slow FP64 CPU implementation of what the CUDA path computes (dense MFIE
 fill with independently integrated self/near entries, dense LU with partial
-pivoting, solve, far field) plus an independent Mie series (``oracle.mie``).
+pivoting, solve, far field), the dense N-Mueller system of a dielectric body
+(``MullerOracle``), independent Mie series for PEC and dielectric spheres
+(``oracle.mie``) and the rank-predictor MLP (``oracle.mlp``).
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package; the library itself never does.
 
@@ -67,6 +69,13 @@ def lib():
         L.or_gauss_legendre.argtypes = [i32, P, P]
         L.or_cheb_cardinal.argtypes = [i32, P, f64, P]
         L.or_patch_point.argtypes = [P, i32, f64, f64, P, P, P]
+        L.or_set_dielectric.argtypes = [P, f64, f64]
+        L.or_muller_near_block.argtypes = [P, i32, i32, P]
+        L.or_muller_far_block.argtypes = [P, i32, i32, P]
+        L.or_matrix_dense_muller.argtypes = [P, P]
+        L.or_rhs_muller.argtypes = [P, i32, P, P, P]
+        L.or_currents_muller.argtypes = [P, P, P, P]
+        L.or_farfield_muller.argtypes = [P, P, i32, P, P, P]
         _lib = L
     return _lib
 
@@ -221,3 +230,58 @@ class Oracle:
             raise np.linalg.LinAlgError("oracle: singular pivot %d" % info)
         X = zgetrs(LU, ipiv, np.asarray(b).T)
         return X.T.copy(), A
+
+
+class MullerOracle(Oracle):
+    """Dense N-Mueller discretisation (Sec. II.A, Eqs. 7-9) of dielectric cube-mapped
+    ellipsoids of relative permittivity eps_r (mu_r = 1) in free space.
+
+    Unknowns per node: (eta0 J^u, eta0 J^v, M^u, M^v) (F = sqrt|G| x contravariant
+    component, Eq. 11); rows per node: tested E equation (u, v), tested H equation (u, v).
+    """
+
+    def __init__(self, bodies, ms, nc, k, eps_r, delta=0.5, q=12, qd=20):
+        super().__init__(bodies, ms, nc, k, delta=delta, q=q, qd=qd)
+        self.eps_r = complex(eps_r)
+        lib().or_set_dielectric(self._h, self.eps_r.real, self.eps_r.imag)
+        self.N = 4 * self.nnode
+
+    def near_block(self, tn, p):
+        W = np.zeros((16, self.nc * self.nc), dtype=np.complex128)
+        lib().or_muller_near_block(self._h, int(tn), int(p), _p(W))
+        return W
+
+    def far_block(self, tn, p):
+        W = np.zeros((16, self.nc * self.nc), dtype=np.complex128)
+        lib().or_muller_far_block(self._h, int(tn), int(p), _p(W))
+        return W
+
+    def dense(self):
+        A = np.zeros((self.N, self.N), dtype=np.complex128, order="F")
+        lib().or_matrix_dense_muller(self._h, _p(A))
+        return A
+
+    def rhs(self, kdirs, pols):
+        kd = np.ascontiguousarray(np.asarray(kdirs, dtype=np.float64).reshape(-1, 3))
+        po = np.ascontiguousarray(np.asarray(pols, dtype=np.float64).reshape(-1, 3))
+        b = np.zeros((kd.shape[0], self.N), dtype=np.complex128)
+        lib().or_rhs_muller(self._h, kd.shape[0], _p(kd), _p(po), _p(b))
+        return b
+
+    def currents(self, x):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+        J = np.zeros((self.nnode, 3), dtype=np.complex128)
+        M = np.zeros((self.nnode, 3), dtype=np.complex128)
+        lib().or_currents_muller(self._h, _p(x), _p(J), _p(M))
+        return J, M
+
+    def farfield(self, x, dirs):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+        ef = np.zeros((d.shape[0], 3), dtype=np.complex128)
+        rcs = np.zeros(d.shape[0])
+        lib().or_farfield_muller(self._h, _p(x), d.shape[0], _p(d), _p(ef), _p(rcs))
+        return ef, rcs
+
+    def matrix_rows(self, rows):
+        raise NotImplementedError("row sampling is provided for the MFIE system only")

@@ -209,6 +209,10 @@ typedef struct {
     int q, qd;
     double *glx, *glw, *gdx, *gdw; /* on [0,1] */
     double accept;     /* box acceptance ratio: dist >= accept * radius */
+    /* dielectric body (N-Mueller formulation): relative permittivity of the interior and
+     * its wavenumber k2 = k sqrt(eps_r); mu_r = 1 */
+    int dielectric;
+    cplx epsr, k2;
 } or_ctx;
 
 static void ctx_patch_map(const or_ctx *c, int p, double u, double v, double *r, double *ru, double *rv)
@@ -375,11 +379,13 @@ void or_patch_point(const or_ctx *c, int p, double u, double v, double *r, doubl
 /* Kernels                                                                    */
 /* ------------------------------------------------------------------------- */
 
-enum { KIND_SINGLE = 0, KIND_MFIE = 1 };
+enum { KIND_SINGLE = 0, KIND_MFIE = 1, KIND_MULLER = 2 };
 
 typedef struct {
     const or_ctx *c;
-    int kind;      /* KIND_SINGLE: G sqrtG (single-layer, Eq. 3); KIND_MFIE: 4 tested components */
+    int kind;      /* KIND_SINGLE: G sqrtG (single-layer, Eq. 3); KIND_MFIE: 4 tested components;
+                      KIND_MULLER: 16 components (4 tested rows x 4 source currents) */
+    double kbox;   /* wavenumber that sizes the adaptive boxes (the largest of the media) */
     int p;         /* source patch */
     double k;
     double tgt[3], tu[3], tv[3];
@@ -400,11 +406,106 @@ static void integ_map(const integ *ig, double u, double v, double *r, double *ru
     }
 }
 
+/* Cardinal functions ell_l(x) (Eq. 12 with Eq. 13) and their derivatives:
+ * ell_l'(x) = sum_{n>=1} (alpha_n / N) T_n(x_l) T_n'(x),  T_n' = n U_{n-1}. */
+static void cheb_cardinal_d(int n, const double *nodes, double x, double *ell, double *dell)
+{
+    double tx[64], dtx[64], tl[64], ux[64];
+    cheb_T(n, x, tx);
+    ux[0] = 1.0;
+    if (n > 1) ux[1] = 2.0 * x;
+    for (int j = 2; j < n; ++j) ux[j] = 2.0 * x * ux[j - 1] - ux[j - 2];
+    dtx[0] = 0.0;
+    for (int j = 1; j < n; ++j) dtx[j] = j * ux[j - 1];
+    for (int l = 0; l < n; ++l) {
+        cheb_T(n, nodes[l], tl);
+        double s = tl[0] * tx[0] / n, ds = 0.0;
+        for (int j = 1; j < n; ++j) {
+            s += 2.0 * tl[j] * tx[j] / n;
+            ds += 2.0 * tl[j] * dtx[j] / n;
+        }
+        ell[l] = s;
+        dell[l] = ds;
+    }
+}
+
+/* N-Mueller integrand at one source point r' = r_p(u,v) for target r_i (Sec. II.A,
+ * Eqs. 2, 7-9 with alpha = -eps_r, beta = -1), tested with sqrt|G| a^b (Eqs. 17-18),
+ * i.e. with t_u = -a_v(r_i), t_v = a_u(r_i) applied to the vector inside n x [ ].
+ * Unknowns (dimensionless scaling): Jbar = eta0 J and M, both as F^a = sqrt|G| x
+ * contravariant component (Eq. 11).  Kernels, R = r_i - r':
+ *   K_S = G1 - eps_r G2,  grad(G1 - G2) = gD R,  grad(G1 - eps_r G2) = gE R,
+ *   g_k = -(1 + j k R) exp(-j k R) / (4 pi R^3)  (grad G_k = g_k R, Eq. 4).
+ * Component [row][col], rows (E-u, E-v, H-u, H-v), cols (J^u, J^v, M^u, M^v):
+ *   E-row b, J^a:  j k K_S (t_b.a_a) ell - (1/(j k)) gD (t_b.R) d_a ell
+ *   E-row b, M^a:  gE t_b.(R x a_a) ell
+ *   H-row b, J^a: -gD t_b.(R x a_a) ell
+ *   H-row b, M^a:  j k K_S (t_b.a_a) ell - (1/(j k)) gD (t_b.R) d_a ell
+ * (the difference kernels carry the cancellation of the strong singularity). */
+static void muller_point(integ *ig, const double *r, const double *ru, const double *rv, double u, double v,
+                         double wt)
+{
+    const or_ctx *c = ig->c;
+    double d[3] = {ig->tgt[0] - r[0], ig->tgt[1] - r[1], ig->tgt[2] - r[2]};
+    double R = norm3(d);
+    double k = ig->k;
+    cplx k2 = c->k2, er = c->epsr;
+    cplx e1 = cexp(-I * k * R), e2 = cexp(-I * k2 * R);
+    cplx G1 = e1 / (4.0 * OR_PI * R), G2 = e2 / (4.0 * OR_PI * R);
+    cplx g1 = -(1.0 + I * k * R) * e1 / (4.0 * OR_PI * R * R * R);
+    cplx g2 = -(1.0 + I * k2 * R) * e2 / (4.0 * OR_PI * R * R * R);
+    cplx KS = G1 - er * G2, gD = g1 - g2, gE = g1 - er * g2;
+    double t[2][3], a[2][3];
+    for (int q = 0; q < 3; ++q) {
+        t[0][q] = -ig->tv[q];
+        t[1][q] = ig->tu[q];
+        a[0][q] = ru[q];
+        a[1][q] = rv[q];
+    }
+    cplx cl[16], cd[16];
+    for (int b = 0; b < 2; ++b) {
+        double tR = dot3(t[b], d);
+        for (int aa = 0; aa < 2; ++aa) {
+            double ta = dot3(t[b], a[aa]);
+            double cr[3];
+            cross3(d, a[aa], cr);
+            double tc = dot3(t[b], cr);
+            cplx sl = I * k * KS * ta, sd = -(1.0 / (I * k)) * gD * tR;
+            cl[(0 + b) * 4 + aa] = sl;           /* E-row b, J^a */
+            cd[(0 + b) * 4 + aa] = sd;
+            cl[(0 + b) * 4 + 2 + aa] = gE * tc;  /* E-row b, M^a */
+            cd[(0 + b) * 4 + 2 + aa] = 0;
+            cl[(2 + b) * 4 + aa] = -gD * tc;     /* H-row b, J^a */
+            cd[(2 + b) * 4 + aa] = 0;
+            cl[(2 + b) * 4 + 2 + aa] = sl;       /* H-row b, M^a */
+            cd[(2 + b) * 4 + 2 + aa] = sd;
+        }
+    }
+    int nc = c->nc;
+    double lu[64], dlu[64], lv[64], dlv[64];
+    cheb_cardinal_d(nc, c->nodes1d, u, lu, dlu);
+    cheb_cardinal_d(nc, c->nodes1d, v, lv, dlv);
+    for (int cmp = 0; cmp < 16; ++cmp) {
+        cplx kl = cl[cmp] * wt, kd = cd[cmp] * wt;
+        int src_dir = cmp & 1; /* a = u (0) or v (1): the derivative of the divergence term */
+        cplx *Wc = ig->W + (size_t)cmp * nc * nc;
+        for (int kb = 0; kb < nc; ++kb)
+            for (int la = 0; la < nc; ++la) {
+                double dl = src_dir == 0 ? dlu[la] * lv[kb] : lu[la] * dlv[kb];
+                Wc[kb * nc + la] += kl * lu[la] * lv[kb] + kd * dl;
+            }
+    }
+}
+
 /* Accumulate one quadrature point (u,v) with weight wt. */
 static void integ_point(integ *ig, double u, double v, double wt)
 {
     double r[3], ru[3], rv[3];
     integ_map(ig, u, v, r, ru, rv);
+    if (ig->kind == KIND_MULLER) {
+        muller_point(ig, r, ru, rv, u, v, wt);
+        return;
+    }
     double d[3] = {ig->tgt[0] - r[0], ig->tgt[1] - r[1], ig->tgt[2] - r[2]};
     double R = norm3(d);
     cplx kv[4];
@@ -468,7 +569,7 @@ static void integ_box(integ *ig, double u0, double u1, double v0, double v1, int
     }
     double dt[3] = {ig->tgt[0] - rc[0], ig->tgt[1] - rc[1], ig->tgt[2] - rc[2]};
     double dist = norm3(dt);
-    int ok = (depth >= 1) && (dist >= ig->c->accept * rad) && (ig->k * rad <= 1.5);
+    int ok = (depth >= 1) && (dist >= ig->c->accept * rad) && (ig->kbox * rad <= 1.5);
     if (ok || depth >= 40) {
         integ_gl_box(ig, u0, u1, v0, v1);
         return;
@@ -551,6 +652,7 @@ void or_near_block(const or_ctx *c, int tn, int p, cplx *W)
     ig.kind = KIND_MFIE;
     ig.p = p;
     ig.k = c->k;
+    ig.kbox = c->k;
     ig.ncomp = 4;
     ig.W = W;
     for (int d = 0; d < 3; ++d) {
@@ -575,6 +677,7 @@ void or_single_layer_block(const or_ctx *c, int tn, int p, cplx *W)
     ig.kind = KIND_SINGLE;
     ig.p = p;
     ig.k = c->k;
+    ig.kbox = c->k;
     ig.ncomp = 1;
     ig.W = W;
     for (int d = 0; d < 3; ++d) ig.tgt[d] = c->nr[3 * tn + d];
@@ -599,6 +702,7 @@ void or_planar_single_layer(const or_ctx *c, double a, double b, double k, const
     ig.pa = a;
     ig.pb = b;
     ig.k = k;
+    ig.kbox = k;
     ig.ncomp = 1;
     ig.W = W;
     for (int d = 0; d < 3; ++d) ig.tgt[d] = tgt[d];
@@ -720,6 +824,168 @@ void or_single_layer_dense(const or_ctx *c, cplx *S)
             }
         }
         free(W);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dielectric body: N-Mueller system (Sec. II.A, Eqs. 7-9)                    */
+/* ------------------------------------------------------------------------- */
+
+/* Interior medium of relative permittivity eps_r (mu_r = 1): k2 = k sqrt(eps_r). */
+void or_set_dielectric(or_ctx *c, double eps_re, double eps_im)
+{
+    c->dielectric = 1;
+    c->epsr = eps_re + I * eps_im;
+    c->k2 = c->k * csqrt(c->epsr);
+    if (cimag(c->k2) > 0) c->k2 = conj(c->k2); /* decaying exp(-j k2 R) for a lossy interior */
+}
+
+static void muller_setup(const or_ctx *c, integ *ig, int tn, int p, cplx *W)
+{
+    memset(ig, 0, sizeof(*ig));
+    ig->c = c;
+    ig->kind = KIND_MULLER;
+    ig->p = p;
+    ig->k = c->k;
+    ig->kbox = fmax(c->k, cabs(c->k2));
+    ig->ncomp = 16;
+    ig->W = W;
+    for (int d = 0; d < 3; ++d) {
+        ig->tgt[d] = c->nr[3 * tn + d];
+        ig->tu[d] = c->nau[3 * tn + d];
+        ig->tv[d] = c->nav[3 * tn + d];
+    }
+}
+
+/* Self/near N-Mueller weights of target node tn over source patch p: the exact
+ * integrals of the integrand against the Chebyshev interpolant (Eq. 20), by the
+ * independent adaptive integrator.  W[(row * 4 + col) * nc^2 + j]. */
+void or_muller_near_block(const or_ctx *c, int tn, int p, cplx *W)
+{
+    integ ig;
+    muller_setup(c, &ig, tn, p, W);
+    int nc = c->nc;
+    if (tn / (nc * nc) == p)
+        integ_patch(&ig, tn % nc, (tn / nc) % nc);
+    else
+        integ_patch(&ig, -1, -1);
+}
+
+/* Far N-Mueller weights: Fejer's rule on the source patch's own nodes (the Nystrom
+ * rule), applied to the same integrand; the divergence terms pick up the spectral
+ * derivative of the interpolant along the node's grid line. */
+void or_muller_far_block(const or_ctx *c, int tn, int p, cplx *W)
+{
+    integ ig;
+    muller_setup(c, &ig, tn, p, W);
+    int nc = c->nc;
+    memset(W, 0, sizeof(cplx) * 16 * nc * nc);
+    for (int kv = 0; kv < nc; ++kv)
+        for (int lu = 0; lu < nc; ++lu)
+            integ_point(&ig, c->nodes1d[lu], c->nodes1d[kv], c->fejer[lu] * c->fejer[kv]);
+}
+
+/* The four rows (E-u, E-v, H-u, H-v) of target node i, length N = 4 nnode, unknown
+ * 4 n + col with col = (Jbar^u, Jbar^v, M^u, M^v); identity terms from the jump
+ * relations (Eq. 6): -(1 + eps_r)/2 on M in the E-rows, (1 + 1)/2 on J in the H-rows. */
+static void node_rows_muller(const or_ctx *c, int i, cplx *rows, cplx *W)
+{
+    int nc = c->nc, nc2 = nc * nc, N = 4 * c->nnode;
+    int ti = i / nc2;
+    for (int p = 0; p < c->npatch; ++p) {
+        if (c->near[(size_t)ti * c->npatch + p])
+            or_muller_near_block(c, i, p, W);
+        else
+            or_muller_far_block(c, i, p, W);
+        for (int row = 0; row < 4; ++row)
+            for (int col = 0; col < 4; ++col)
+                for (int j = 0; j < nc2; ++j)
+                    rows[(size_t)row * N + 4 * (p * nc2 + j) + col] = W[(row * 4 + col) * nc2 + j];
+    }
+    cplx ide = -(1.0 + c->epsr) / 2.0;
+    rows[(size_t)0 * N + 4 * i + 2] += ide;
+    rows[(size_t)1 * N + 4 * i + 3] += ide;
+    rows[(size_t)2 * N + 4 * i + 0] += 1.0;
+    rows[(size_t)3 * N + 4 * i + 1] += 1.0;
+}
+
+/* Dense N-Mueller matrix, column-major A[col * N + row], N = 4 nnode. */
+void or_matrix_dense_muller(const or_ctx *c, cplx *A)
+{
+    int N = 4 * c->nnode;
+    int nc2 = c->nc * c->nc;
+#pragma omp parallel
+    {
+        cplx *rows = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)N);
+        cplx *W = (cplx *)malloc(sizeof(cplx) * 16 * nc2);
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < c->nnode; ++i) {
+            node_rows_muller(c, i, rows, W);
+            for (int col = 0; col < N; ++col)
+                for (int r = 0; r < 4; ++r) A[(size_t)col * N + 4 * i + r] = rows[(size_t)r * N + col];
+        }
+        free(rows);
+        free(W);
+    }
+}
+
+/* N-Mueller right-hand sides for E = pol exp(-jk khat.r): E-row b: t_b . E_inc,
+ * H-row b: t_b . (eta0 H_inc) = t_b . (khat x pol) exp(-jk khat.r); b [nrhs][4 nnode]. */
+void or_rhs_muller(const or_ctx *c, int nrhs, const double *kdir, const double *pol, cplx *b)
+{
+    int N = 4 * c->nnode;
+    for (int r = 0; r < nrhs; ++r) {
+        double kh[3], h0[3];
+        const double *po = pol + 3 * r;
+        for (int d = 0; d < 3; ++d) kh[d] = kdir[3 * r + d];
+        cross3(kh, po, h0);
+        for (int i = 0; i < c->nnode; ++i) {
+            cplx ph = cexp(-I * c->k * dot3(kh, c->nr + 3 * i));
+            const double *au = c->nau + 3 * i, *av = c->nav + 3 * i;
+            cplx *o = b + (size_t)r * N + 4 * i;
+            o[0] = -dot3(av, po) * ph;
+            o[1] = dot3(au, po) * ph;
+            o[2] = -dot3(av, h0) * ph;
+            o[3] = dot3(au, h0) * ph;
+        }
+    }
+}
+
+/* J (A/m) and M (V/m) at the nodes from an N-Mueller solution x[4 nnode]. */
+void or_currents_muller(const or_ctx *c, const cplx *x, cplx *J, cplx *M)
+{
+    for (int i = 0; i < c->nnode; ++i)
+        for (int d = 0; d < 3; ++d) {
+            J[3 * i + d] = (x[4 * i] * c->nau[3 * i + d] + x[4 * i + 1] * c->nav[3 * i + d]) / c->nsg[i] / c->eta0;
+            M[3 * i + d] = (x[4 * i + 2] * c->nau[3 * i + d] + x[4 * i + 3] * c->nav[3 * i + d]) / c->nsg[i];
+        }
+}
+
+/* Far field of an N-Mueller solution: with N_J = sum_j w_j (Jbar^u a_u + Jbar^v a_v)_j
+ * exp(jk rhat.r_j) and N_M likewise from M,
+ *   E_far = -jk/(4 pi) [ (I - rhat rhat) N_J - rhat x N_M ],  rcs = 4 pi |E_far|^2. */
+void or_farfield_muller(const or_ctx *c, const cplx *x, int nang, const double *obs, cplx *efar, double *rcs)
+{
+    for (int a = 0; a < nang; ++a) {
+        const double *rh = obs + 3 * a;
+        cplx NJ[3] = {0, 0, 0}, NM[3] = {0, 0, 0};
+        for (int j = 0; j < c->nnode; ++j) {
+            cplx ph = cexp(I * c->k * dot3(rh, c->nr + 3 * j)) * c->nw[j];
+            for (int d = 0; d < 3; ++d) {
+                NJ[d] += ph * (x[4 * j] * c->nau[3 * j + d] + x[4 * j + 1] * c->nav[3 * j + d]);
+                NM[d] += ph * (x[4 * j + 2] * c->nau[3 * j + d] + x[4 * j + 3] * c->nav[3 * j + d]);
+            }
+        }
+        cplx rn = rh[0] * NJ[0] + rh[1] * NJ[1] + rh[2] * NJ[2];
+        cplx rxm[3] = {rh[1] * NM[2] - rh[2] * NM[1], rh[2] * NM[0] - rh[0] * NM[2], rh[0] * NM[1] - rh[1] * NM[0]};
+        cplx pre = -I * c->k / (4.0 * OR_PI);
+        double s = 0;
+        for (int d = 0; d < 3; ++d) {
+            cplx e = pre * (NJ[d] - rn * rh[d] - rxm[d]);
+            efar[3 * a + d] = e;
+            s += creal(e) * creal(e) + cimag(e) * cimag(e);
+        }
+        rcs[a] = 4.0 * OR_PI * s;
     }
 }
 
