@@ -253,6 +253,20 @@ const char *hm_mlp_last_error(hm_mlp m);
 void hm_mlp_destroy(hm_mlp m);
 void hm_destroy(hm_handle h);
 
+/* ---- host-only planning (no GPU needed) ------------------------------------ */
+
+/* The cluster tree and block cluster tree that hm_build_geometry builds (Sec. III:
+ * balanced median bisection along the widest bounding-box axis, leaf clusters of at
+ * most `leaf` unknowns; admissibility of Eq. 21, min(diam) <= eta dist of the
+ * bounding boxes, dist > 0), computed on the host from node positions xyz [nnode][3]
+ * (two unknowns per node, interleaved).  *nblocks receives the number of leaves;
+ * blocks (may be NULL) receives [nblocks][5] = type (0 dense, 1 admissible), row0,
+ * nrow, col0, ncol in tree-ordered unknowns; perm_node (may be NULL) [nnode] receives
+ * the natural node at each tree position.  Blocks are those before ACA, which may
+ * split an admissible block further. */
+hm_status hm_plan_host(const double *xyz, int nnode, int leaf, double eta, int *nblocks, int *blocks,
+                       int *perm_node);
+
 /* ---- inspection (tests and diagnostics; all synchronise) ------------------- */
 
 /* Node table, host double [nnode][14]: r[3], a_u[3], a_v[3], n[3], sqrtG, w. */

@@ -223,6 +223,7 @@ void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n);
 // ---- hm_planner.cpp ----
 void plan_geometry(hm_handle_s *h);  // nodes, near pairs, cluster tree, block tree
 void rebuild_block_tree(hm_handle_s *h);  // block tree from the cluster tree (discards blocks)
+void build_cluster_tree(hm_handle_s *h);  // cluster tree from h->h_nodes (host only)
 void cheb_nodes_host(int n, double *x);
 void fejer_weights_host(int n, double *w);
 void gauss_legendre_host(int q, double *x, double *w);

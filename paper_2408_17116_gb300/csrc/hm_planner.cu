@@ -221,14 +221,7 @@ void plan_geometry(hm_handle_s *h)
     HM_CUDA(cudaMemcpyAsync(h->d_nearidx, nearidx.data(), sizeof(int) * nearidx.size(), cudaMemcpyHostToDevice, h->stream));
     HM_CUDA(cudaMemcpyAsync(h->d_pair_q, h->pair_q.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, h->stream));
     HM_CUDA(cudaMemcpyAsync(h->d_pair_p, h->pair_p.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, h->stream));
-    // cluster tree: balanced median bisection to a common leaf depth
-    int depth = 0;
-    while (2 * ((h->nnode + (1 << depth) - 1) >> depth) > h->prm.leaf && (1 << depth) < h->nnode) ++depth;
-    h->perm_node.resize(h->nnode);
-    std::iota(h->perm_node.begin(), h->perm_node.end(), 0);
-    h->clusters.clear();
-    int root;
-    build_clusters(h, 0, h->nnode, 0, depth, root);
+    build_cluster_tree(h);
     std::vector<int> perm(h->N), iperm(h->N);
     for (int pos = 0; pos < h->nnode; ++pos)
         for (int c = 0; c < 2; ++c) {
@@ -242,6 +235,54 @@ void plan_geometry(hm_handle_s *h)
     // block cluster tree
     rebuild_block_tree(h);
     HM_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// Cluster tree over the host node table: balanced median bisection along the widest
+// bounding-box axis to a common leaf depth (the first depth whose clusters hold at
+// most n_leaf unknowns, two per node).
+void build_cluster_tree(hm_handle_s *h)
+{
+    int depth = 0;
+    while (2 * ((h->nnode + (1 << depth) - 1) >> depth) > h->prm.leaf && (1 << depth) < h->nnode) ++depth;
+    h->perm_node.resize(h->nnode);
+    std::iota(h->perm_node.begin(), h->perm_node.end(), 0);
+    h->clusters.clear();
+    int root;
+    build_clusters(h, 0, h->nnode, 0, depth, root);
+}
+
+extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int leaf, double eta, int *nblocks, int *blocks,
+                                  int *perm_node)
+{
+    if (!xyz || nnode <= 0 || leaf < 2 || !(eta > 0.0) || !nblocks) return HM_ERR_ARG;
+    try {
+        hm_handle_s h;  // host-only planning: no stream, no device memory
+        h.nnode = nnode;
+        h.N = 2 * nnode;
+        h.prm.leaf = leaf;
+        h.prm.eta = eta;
+        h.h_nodes.assign(14 * (size_t)nnode, 0.0);
+        for (int i = 0; i < nnode; ++i)
+            for (int d = 0; d < 3; ++d) h.h_nodes[(size_t)d * nnode + i] = xyz[3 * (size_t)i + d];
+        build_cluster_tree(&h);
+        rebuild_block_tree(&h);
+        *nblocks = (int)h.leaves.size();
+        if (blocks)
+            for (size_t i = 0; i < h.leaves.size(); ++i) {
+                const Block *b = h.leaves[i];
+                int *o = blocks + 5 * i;
+                o[0] = b->type == B_DENSE ? 0 : 1;
+                o[1] = b->r0;
+                o[2] = b->nr;
+                o[3] = b->c0;
+                o[4] = b->nc;
+            }
+        if (perm_node) std::copy(h.perm_node.begin(), h.perm_node.end(), perm_node);
+        for (Block *b : h.blocks) delete b;
+        return HM_OK;
+    } catch (...) {
+        return HM_ERR_OOM;
+    }
 }
 
 void rebuild_block_tree(hm_handle_s *h)

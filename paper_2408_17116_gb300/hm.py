@@ -31,7 +31,7 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host", "hm_rank_samples",
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
-           "hm_farfield_static")
+           "hm_farfield_static", "hm_plan_host")
 
 
 class hm_params(ctypes.Structure):
@@ -76,6 +76,7 @@ def load(path=SO):
     L.hm_farfield.argtypes = [P, I, P, I, P, P, P]
     L.hm_matvec.argtypes = [P, I, P, P]
     L.hm_farfield_static.argtypes = [P, I, P, I, P, P, P]
+    L.hm_plan_host.argtypes = [P, I, I, D, ctypes.POINTER(I), P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
@@ -108,6 +109,23 @@ def load(path=SO):
 
 def _np_ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def plan_host(xyz, leaf, eta):
+    """Block cluster tree of hm_plan_host (host only): (blocks [n][5], perm_node [nnode])."""
+    L = load()
+    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    n = ctypes.c_int()
+    st = L.hm_plan_host(_np_ptr(xyz), xyz.shape[0], int(leaf), float(eta), ctypes.byref(n), None, None)
+    if st != HM_OK:
+        raise HmError(st, "hm_plan_host")
+    blocks = np.empty((n.value, 5), dtype=np.int32)
+    perm = np.empty(xyz.shape[0], dtype=np.int32)
+    st = L.hm_plan_host(_np_ptr(xyz), xyz.shape[0], int(leaf), float(eta), ctypes.byref(n), _np_ptr(blocks),
+                        _np_ptr(perm))
+    if st != HM_OK:
+        raise HmError(st, "hm_plan_host")
+    return blocks, perm
 
 
 def make_bodies(bodies, ms):

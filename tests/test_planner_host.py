@@ -1,0 +1,68 @@
+"""The block cluster tree (Sec. III, Eq. 21) built on the host by hm_plan_host, the
+same planner hm_build_geometry runs: the permutation is a bijection, the leaves tile
+the matrix exactly once, every admissible leaf satisfies Eq. 21 on the bounding boxes
+of its clusters, every dense leaf is a leaf-cluster pair that is not admissible, and
+the leaf clusters are balanced and no larger than n_leaf.  No GPU is needed."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_17116_gb300 import hm, workloads
+
+
+def _geometry(name):
+    wl = workloads.workload(name)
+    o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
+    return o.node_table()[:, :3], wl
+
+
+def _bbox(pts):
+    return pts.min(0), pts.max(0)
+
+
+def _dist_diam(p1, p2):
+    (a0, a1), (b0, b1) = _bbox(p1), _bbox(p2)
+    gap = np.maximum(0.0, np.maximum(a0 - b1, b0 - a1))
+    return np.linalg.norm(gap), min(np.linalg.norm(a1 - a0), np.linalg.norm(b1 - b0))
+
+
+@pytest.mark.parametrize("name", ["sphere_d2_m2_nc6", "ellipsoid_small", "sphere_d4_m2_nc10"])
+def test_block_tree_invariants(name):
+    xyz, wl = _geometry(name)
+    leaf, eta = wl["leaf"], wl["eta"]
+    blocks, perm = hm.plan_host(xyz, leaf, eta)
+    n = xyz.shape[0]
+    N = 2 * n
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    # exact tiling of the N x N matrix
+    cover = np.zeros((N, N), dtype=np.int16)
+    for typ, r0, nr, c0, nc in blocks:
+        assert r0 % 2 == 0 and nr % 2 == 0 and c0 % 2 == 0 and nc % 2 == 0  # nodes stay whole
+        cover[r0:r0 + nr, c0:c0 + nc] += 1
+    assert (cover == 1).all()
+    pts = xyz[perm]
+    sizes = set()
+    for typ, r0, nr, c0, nc in blocks:
+        pr, pc = pts[r0 // 2:(r0 + nr) // 2], pts[c0 // 2:(c0 + nc) // 2]
+        dist, dmin = _dist_diam(pr, pc)
+        if typ == 1:
+            assert dist > 0 and dmin <= eta * dist * (1 + 1e-12)
+        else:
+            assert not (dist > 0 and dmin <= eta * dist * (1 - 1e-12))
+            assert nr <= leaf and nc <= leaf
+            sizes.update((nr, nc))
+    assert max(sizes) - min(sizes) <= 2  # balanced bisection: leaf clusters differ by one node at most
+    assert (blocks[:, 0] == 1).sum() > 0
+
+
+def test_no_admissible_blocks_when_eta_is_tiny():
+    xyz, wl = _geometry("sphere_d2_m2_nc6")
+    blocks, _ = hm.plan_host(xyz, wl["leaf"], 1e-9)
+    assert (blocks[:, 0] == 0).all()
+
+
+def test_rejects_bad_arguments():
+    with pytest.raises(hm.HmError):
+        hm.plan_host(np.zeros((0, 3)), 64, 2.0)
+    with pytest.raises(hm.HmError):
+        hm.plan_host(np.random.default_rng(0).random((10, 3)), 1, 2.0)
