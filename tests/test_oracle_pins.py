@@ -315,3 +315,19 @@ def test_mie_low_frequency_current():
         J = mie.pec_surface_current(k, a, th, ph, oracle.ETA0)
         Jref = 1.5 * np.cross(n, [0, 1 / oracle.ETA0, 0])
         assert np.linalg.norm(J - Jref) < 1e-3 * np.linalg.norm(Jref)  # O(ka) correction
+
+
+def test_mfie_converges_spectrally_to_mie_in_the_chebyshev_order():
+    # p-refinement on the 1-wavelength sphere: the current error against Mie falls by an
+    # order of magnitude or more from Nc = 5 to Nc = 7 to Nc = 9
+    wl = workloads.workload("sphere_d1_m1_nc8")
+    a, k = wl["radius"], wl["k"]
+    errs = []
+    for nc in (5, 7, 9):
+        o = oracle.Oracle(wl["bodies"], wl["ms"], nc, k)
+        x, _ = o.solve_dense(o.rhs(wl["kdirs"], wl["pols"]))
+        T, Jm = _mie_currents(o, k, a)
+        J = o.currents(x[0])
+        w = T[:, 12] * T[:, 13]
+        errs.append(np.sqrt(np.sum(w[:, None] * np.abs(J - Jm) ** 2) / np.sum(w[:, None] * np.abs(Jm) ** 2)))
+    assert errs[1] < 0.1 * errs[0] and errs[2] < 0.1 * errs[1], errs
