@@ -2,7 +2,8 @@
 eps_r = 1 every kernel term cancels and the solution is the incident field's
 equivalent currents; the dense solution converges spectrally to the dielectric Mie
 series (surface currents J, M and the bistatic RCS); the self/near integrals are
-converged in the integrator's quadrature orders."""
+converged in the integrator's quadrature orders; and the discrete solutions of both
+oracles (MFIE and N-Mueller) satisfy the optical theorem."""
 import numpy as np
 import pytest
 
@@ -79,3 +80,35 @@ def test_near_integrals_converged_in_quadrature_order():
     for tn, p in [(27, 0), (0, 0), (27, 2), (63, 1)]:
         a, c = lo.near_block(tn, p), hi.near_block(tn, p)
         assert np.max(np.abs(a - c)) <= 1e-8 * np.max(np.abs(c)), (tn, p)
+
+
+def _sphere_directions(nmu=24, nph=48):
+    mu, wmu = np.polynomial.legendre.leggauss(nmu)
+    ph = 2 * np.pi * np.arange(nph) / nph
+    st = np.sqrt(1 - mu * mu)
+    dirs = np.stack([np.outer(st, np.cos(ph)).ravel(), np.outer(st, np.sin(ph)).ravel(), np.repeat(mu, nph)], 1)
+    return dirs, np.repeat(wmu, nph) * 2 * np.pi / nph
+
+
+@pytest.mark.parametrize("kind", ["pec_mfie", "dielectric_muller"])
+def test_optical_theorem_of_the_discrete_solution(kind):
+    # lossless scatterers: the power scattered over all directions equals the power the
+    # forward amplitude removes from the incident wave (exp(j w t): sigma_ext =
+    # -(4 pi / k) Im(pol . E_far(khat))); both equal the Mie cross section
+    kh, po = workloads.axial_incidence()
+    if kind == "pec_mfie":
+        wl = workloads.workload("sphere_d1_m1_nc8")
+        o = oracle.Oracle(wl["bodies"], wl["ms"], 8, K)
+        x = o.solve_dense(o.rhs(kh, po))[0][0]
+        ref = mie.pec_cross_sections(K, wl["radius"])[0]
+    else:
+        o = _sphere(0.25, 1, 8, 2.25)
+        x = _solve(o)
+        ref = mie.dielectric_cross_sections(K, 0.25, 1.5)[0]
+    dirs, w = _sphere_directions()
+    ef, _ = o.farfield(x, dirs)
+    sca = np.sum(w * np.sum(np.abs(ef) ** 2, 1))
+    ef0, _ = o.farfield(x, kh)
+    ext = -(4 * np.pi / K) * np.imag(ef0[0] @ po[0])
+    assert abs(sca - ext) < 1e-4 * sca, (sca, ext)
+    assert abs(sca - ref) < 1e-4 * ref and abs(ext - ref) < 1e-4 * ref, (sca, ext, ref)
