@@ -66,3 +66,24 @@ def test_rejects_bad_arguments():
         hm.plan_host(np.zeros((0, 3)), 64, 2.0)
     with pytest.raises(hm.HmError):
         hm.plan_host(np.random.default_rng(0).random((10, 3)), 1, 2.0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33])
+def test_degenerate_and_tiny_inputs(n):
+    # coincident points: zero distances, so nothing is admissible; the tiling still holds
+    xyz = np.zeros((n, 3))
+    blocks, perm = hm.plan_host(xyz, 4, 2.0)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    assert (blocks[:, 0] == 0).all()
+    cover = np.zeros((2 * n, 2 * n), dtype=np.int16)
+    for typ, r0, nr, c0, nc in blocks:
+        cover[r0:r0 + nr, c0:c0 + nc] += 1
+    assert (cover == 1).all()
+
+
+def test_collinear_points_split_along_the_line():
+    xyz = np.stack([np.linspace(0, 10, 200), np.zeros(200), np.zeros(200)], 1)
+    blocks, perm = hm.plan_host(xyz, 16, 2.0)
+    # bisection along x keeps the order of the line (up to the tie rule)
+    assert np.array_equal(perm, np.arange(200))
+    assert (blocks[:, 0] == 1).any()
