@@ -99,7 +99,7 @@ def load_workload(name):
     return workloads.workload(name)
 
 
-def cpu_baseline(wl, budget_s=20.0):
+def cpu_baseline(wl):
     """The oracle as it stands, on a bounded sample of the workload, scaled to unknowns/s.
 
     Sample: dense MFIE fill of R rows of the full matrix, and the oracle's dense LU +

@@ -138,7 +138,9 @@ enum {
 const char *hm_version(void);
 
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*; may be NULL)
- * on the current device. */
+ * on the current device.  The library allocates its internal buffers with
+ * cudaMallocAsync from the device's default memory pool and sets that pool's release
+ * threshold to keep freed memory cached (a process-wide setting of that pool). */
 hm_status hm_create(hm_handle *h, void *cuda_stream);
 
 /* Build the discretisation: node geometry at first-kind Chebyshev nodes (Sec. II.B,
