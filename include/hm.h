@@ -269,6 +269,17 @@ void hm_destroy(hm_handle h);
 hm_status hm_plan_host(const double *xyz, int nnode, int leaf, double eta, int *nblocks, int *blocks,
                        int *perm_node);
 
+/* N-Mueller formulation of a dielectric body (Sec. II.A, Eqs. 7-9 with
+ * alpha = -eps_r, beta = -1, mu_r = 1): the far (Nystrom) entries of target node tn
+ * over every node of source patch p, evaluated on the host with the library's geometry
+ * and the entry generator its device fill uses.  out: host complex128 [16][Nc^2],
+ * index (row * 4 + col) * Nc^2 + j; rows E-u, E-v, H-u, H-v (tested with sqrt|G| a^b),
+ * columns eta0 J^u, eta0 J^v, M^u, M^v of source node j; relative permittivity
+ * eps_re + j eps_im of the interior (Im <= 0 for a lossy medium with exp(j w t)).  The
+ * identity terms of the jump relations (Eq. 6) are not included. */
+hm_status hm_muller_far_block_host(const hm_body *bodies, int nbodies, int nodes_per_dir, double k0,
+                                   double eps_re, double eps_im, int tn, int p, void *out);
+
 /* ---- inspection (tests and diagnostics; all synchronise) ------------------- */
 
 /* Node table, host double [nnode][14]: r[3], a_u[3], a_v[3], n[3], sqrtG, w. */

@@ -70,7 +70,7 @@ struct DevPatch {
 };
 
 // Face frames (e_f, e1, e2), e1 x e2 = e_f so a_u x a_v is the outward normal.
-__device__ __forceinline__ void face_frame(int f, double *ef, double *e1, double *e2)
+__host__ __device__ __forceinline__ void face_frame(int f, double *ef, double *e1, double *e2)
 {
     ef[0] = ef[1] = ef[2] = 0.0;
     e1[0] = e1[1] = e1[2] = 0.0;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void face_frame(int f, double *ef, double *e1, double
 }
 
 // r(u,v), a_u = dr/du, a_v = dr/dv for patch P of body B (Eq. 14); equiangular cube map.
-__device__ __forceinline__ void patch_eval(const DevBody &B, const DevPatch &P, double u, double v,
+__host__ __device__ __forceinline__ void patch_eval(const DevBody &B, const DevPatch &P, double u, double v,
                                            double *r, double *ru, double *rv)
 {
     const double q = 0.78539816339744830962;  // pi/4
@@ -120,7 +120,7 @@ __device__ __forceinline__ void patch_eval(const DevBody &B, const DevPatch &P, 
 
 // Chart coordinates (u, v) of a surface point x in patch P's extended chart.
 // Returns false when x is not in the half-space of P's cube face (chart undefined).
-__device__ __forceinline__ bool patch_chart(const DevBody &B, const DevPatch &P, const double *x,
+__host__ __device__ __forceinline__ bool patch_chart(const DevBody &B, const DevPatch &P, const double *x,
                                             double *u, double *v)
 {
     double d[3] = {x[0] - B.c[0], x[1] - B.c[1], x[2] - B.c[2]};
@@ -141,7 +141,7 @@ __device__ __forceinline__ bool patch_chart(const DevBody &B, const DevPatch &P,
 }
 
 // T_0..T_{n-1} at x by the three-term recurrence.
-__device__ __forceinline__ void cheb_T(int n, double x, double *t)
+__host__ __device__ __forceinline__ void cheb_T(int n, double x, double *t)
 {
     t[0] = 1.0;
     if (n > 1) t[1] = x;
