@@ -279,6 +279,15 @@ hm_status hm_plan_host(const double *xyz, int nnode, int leaf, double eta, int *
  * identity terms of the jump relations (Eq. 6) are not included. */
 hm_status hm_muller_far_block_host(const hm_body *bodies, int nbodies, int nodes_per_dir, double k0,
                                    double eps_re, double eps_im, int tn, int p, void *out);
+/* The self/near N-Mueller integrals of target node tn over source patch p (Eq. 20: the
+ * integrand against the patch's Chebyshev interpolant), by the near-field rule of the
+ * device quadrature (singular point split, graded tensor panels for near targets, Duffy
+ * squares and graded strips for self targets) evaluated on the host; same layout as
+ * hm_muller_far_block_host.  qd, qi, qo: Gauss points of the Duffy, inner graded and
+ * outer panels (0: 24, 24, 16); t0: inner panel length (0: 0.5). */
+hm_status hm_muller_near_block_host(const hm_body *bodies, int nbodies, int nodes_per_dir, double k0,
+                                    double eps_re, double eps_im, int tn, int p, int qd, int qi, int qo, double t0,
+                                    void *out);
 
 /* ---- inspection (tests and diagnostics; all synchronise) ------------------- */
 

@@ -621,6 +621,18 @@ static void integ_corner_rect(integ *ig, double uc, double vc, double du, double
         integ_box(ig, uc + du1, uc + du, vc, vc + dv, 1);
         return;
     }
+    /* the Duffy square must resolve the kernel's oscillation: larger than 1.5/k in
+     * physical size, it shrinks to that size at the corner and the rest of the
+     * rectangle goes to the adaptive boxes */
+    double side = fmax(a, b);
+    if (ig->kbox * side > 1.5) {
+        double f = 1.5 / (ig->kbox * side);
+        double du1 = du * f, dv1 = dv * f;
+        integ_corner_rect(ig, uc, vc, du1, dv1);
+        integ_box(ig, uc + du1, uc + du, vc, vc + dv, 1);
+        integ_box(ig, uc, uc + du1, vc + dv1, vc + dv, 1);
+        return;
+    }
     integ_duffy(ig, uc, vc, du, dv);
 }
 

@@ -112,3 +112,151 @@ __host__ __device__ inline void muller_far_pair(const double *X, int nnode, int 
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Integrand of the N-Mueller self/near integrals at one source point r' = r(u,v)
+// with tangents a_u, a_v, for target r_i with tangents (tu = a_u(r_i), tv = a_v(r_i)):
+// the coefficients of the cardinal function ell_j (cl) and of its derivative along
+// the source direction of the column (cd, divergence terms only), per unit du dv:
+//   E-row b, J^a: cl = j k K_S (t_b.a_a),  cd = -(1/(j k)) gD (t_b.R)
+//   E-row b, M^a: cl = gE t_b.(R x a_a)
+//   H-row b, J^a: cl = -gD t_b.(R x a_a)
+//   H-row b, M^a: as E-row b, J^a.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void muller_point(const double *ri, const double *tu, const double *tv, const double *r,
+                                             const double *ru, const double *rv, const MullerMedia &md, zc *cl,
+                                             zc *cd)
+{
+    double R3[3] = {ri[0] - r[0], ri[1] - r[1], ri[2] - r[2]};
+    double R = sqrt(R3[0] * R3[0] + R3[1] * R3[1] + R3[2] * R3[2]);
+    zc G1, g1, G2, g2;
+    green_pair(zmake(md.k, 0.0), R, G1, g1);
+    green_pair(md.k2, R, G2, g2);
+    zc KS = zsub(G1, zmul(md.epsr, G2)), gD = zsub(g1, g2), gE = zsub(g1, zmul(md.epsr, g2));
+    const zc jk = zmake(0.0, md.k), inv_jk = zmake(0.0, -1.0 / md.k);
+    double t[2][3] = {{-tv[0], -tv[1], -tv[2]}, {tu[0], tu[1], tu[2]}};
+    const double *a[2] = {ru, rv};
+    for (int b = 0; b < 2; ++b) {
+        double tR = t[b][0] * R3[0] + t[b][1] * R3[1] + t[b][2] * R3[2];
+        zc sd = zmul(inv_jk, zscale(gD, -tR));
+        for (int aa = 0; aa < 2; ++aa) {
+            const double *av = a[aa];
+            double ta = t[b][0] * av[0] + t[b][1] * av[1] + t[b][2] * av[2];
+            double cr[3] = {R3[1] * av[2] - R3[2] * av[1], R3[2] * av[0] - R3[0] * av[2], R3[0] * av[1] - R3[1] * av[0]};
+            double tc = t[b][0] * cr[0] + t[b][1] * cr[1] + t[b][2] * cr[2];
+            zc sl = zscale(zmul(jk, KS), ta);
+            cl[b * 4 + aa] = sl;
+            cd[b * 4 + aa] = sd;
+            cl[b * 4 + 2 + aa] = zscale(gE, tc);
+            cd[b * 4 + 2 + aa] = zmake(0, 0);
+            cl[(2 + b) * 4 + aa] = zscale(gD, -tc);
+            cd[(2 + b) * 4 + aa] = zmake(0, 0);
+            cl[(2 + b) * 4 + 2 + aa] = sl;
+            cd[(2 + b) * 4 + 2 + aa] = sd;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pieces of the self/near quadrature rule on the source patch's parameter square,
+// split at the point (uc, vc) nearest the singularity (the same construction as the
+// MFIE near-field kernel): for a near target (eps > 0) four tensor rectangles with
+// graded axes (a sinh-mapped Gauss panel of length min(L, t0) clustered at the corner
+// on the scale eps, then a plain Gauss panel on [t0, L]); for a self target (eps = 0)
+// on each corner rectangle a Duffy square (two triangles, Jacobian s) on its physically
+// square part and a tensor strip (plain across, graded along) on the remainder.
+// ---------------------------------------------------------------------------
+struct NearAxis {
+    int graded;              // 1: graded (sinh panel + plain panel), 0: plain Gauss
+    double eps, L, start, sgn;
+};
+struct NearPiece {
+    int type;                // 0 tensor (axes A = u, B = v); 1 Duffy u = uc + du s, v = vc + dv s t;
+                             // 2 Duffy v = vc + dv s, u = uc + du s t
+    double uc, vc, du, dv;   // Duffy corner and signed side lengths
+    NearAxis A, B;           // tensor axes
+};
+
+// Returns the number of pieces written to pc (at most 12).  gu, gv: |a_u|, |a_v| at
+// (uc, vc) (they decide the physically square part of a self rectangle).
+__host__ __device__ inline int near_pieces(double uc, double vc, double eps, double gu, double gv, NearPiece *pc)
+{
+    int np = 0;
+    for (int corner = 0; corner < 4; ++corner) {
+        double du = (corner & 1) ? (-1.0 - uc) : (1.0 - uc);
+        double dv = (corner & 2) ? (-1.0 - vc) : (1.0 - vc);
+        if (fabs(du) < 1e-14 || fabs(dv) < 1e-14) continue;
+        double su = du > 0 ? 1.0 : -1.0, sv = dv > 0 ? 1.0 : -1.0;
+        if (eps > 0.0) {
+            NearPiece &p = pc[np++];
+            p.type = 0;
+            p.A = NearAxis{1, eps, fabs(du), uc, su};
+            p.B = NearAxis{1, eps, fabs(dv), vc, sv};
+            continue;
+        }
+        double pa = fabs(du) * gu, pb = fabs(dv) * gv;
+        double ddu = du, ddv = dv;
+        int strip = 0;
+        if (pb > pa) {
+            ddv = sv * pa / gv;
+            if (fabs(dv) - fabs(ddv) > 1e-14) strip = 1;
+        } else {
+            ddu = su * pb / gu;
+            if (fabs(du) - fabs(ddu) > 1e-14) strip = 2;
+        }
+        for (int tri = 1; tri <= 2; ++tri) {
+            NearPiece &p = pc[np++];
+            p.type = tri;
+            p.uc = uc;
+            p.vc = vc;
+            p.du = ddu;
+            p.dv = ddv;
+        }
+        if (strip) {
+            NearPiece &p = pc[np++];
+            p.type = 0;
+            if (strip == 1) {
+                p.A = NearAxis{0, 0.0, fabs(du), uc, su};
+                p.B = NearAxis{1, fabs(ddv), fabs(dv) - fabs(ddv), vc + ddv, sv};
+            } else {
+                p.A = NearAxis{1, fabs(ddu), fabs(du) - fabs(ddu), uc + ddu, su};
+                p.B = NearAxis{0, 0.0, fabs(dv), vc, sv};
+            }
+        }
+    }
+    return np;
+}
+
+// Points and weights of one axis on [0,1]-mapped Gauss tables: gi (qi points) for the
+// graded inner panel and the plain axis, go (qo points) for the outer panel.  Returns
+// the number of points (<= qi + qo).
+__host__ __device__ inline int near_axis_points(const NearAxis &ax, const double *gix, const double *giw, int qi,
+                                                const double *gox, const double *gow, int qo, double t0, double *x,
+                                                double *w)
+{
+    int n = 0;
+    if (!ax.graded) {
+        for (int i = 0; i < qi; ++i) {
+            x[n] = ax.start + ax.sgn * ax.L * gix[i];
+            w[n] = ax.L * giw[i];
+            ++n;
+        }
+        return n;
+    }
+    double Lin = fmin(ax.L, t0);
+    double mu = asinh(Lin / ax.eps);
+    for (int i = 0; i < qi; ++i) {
+        double z = mu * gix[i];
+        x[n] = ax.start + ax.sgn * ax.eps * sinh(z);
+        w[n] = ax.eps * mu * cosh(z) * giw[i];
+        ++n;
+    }
+    if (ax.L > t0) {
+        for (int i = 0; i < qo; ++i) {
+            x[n] = ax.start + ax.sgn * (t0 + (ax.L - t0) * gox[i]);
+            w[n] = (ax.L - t0) * gow[i];
+            ++n;
+        }
+    }
+    return n;
+}

@@ -31,7 +31,7 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host", "hm_rank_samples",
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
-           "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host")
+           "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host")
 
 
 class hm_params(ctypes.Structure):
@@ -78,6 +78,7 @@ def load(path=SO):
     L.hm_farfield_static.argtypes = [P, I, P, I, P, P, P]
     L.hm_plan_host.argtypes = [P, I, I, D, ctypes.POINTER(I), P, P]
     L.hm_muller_far_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, P]
+    L.hm_muller_near_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, I, I, I, D, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
@@ -139,6 +140,19 @@ def muller_far_block_host(bodies, ms, nc, k0, eps_r, tn, p):
                                     _np_ptr(out))
     if st != HM_OK:
         raise HmError(st, "hm_muller_far_block_host")
+    return out
+
+
+def muller_near_block_host(bodies, ms, nc, k0, eps_r, tn, p, qd=0, qi=0, qo=0, t0=0.0):
+    """N-Mueller self/near integrals of target node tn over source patch p (host): [16][nc^2]."""
+    L = load()
+    arr = make_bodies(bodies, ms)
+    out = np.zeros((16, int(nc) ** 2), dtype=np.complex128)
+    eps = complex(eps_r)
+    st = L.hm_muller_near_block_host(arr, len(ms), int(nc), float(k0), eps.real, eps.imag, int(tn), int(p),
+                                     int(qd), int(qi), int(qo), float(t0), _np_ptr(out))
+    if st != HM_OK:
+        raise HmError(st, "hm_muller_near_block_host")
     return out
 
 

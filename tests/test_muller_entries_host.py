@@ -37,3 +37,33 @@ def test_rejects_bad_arguments():
         hm.muller_far_block_host(wl["bodies"], wl["ms"], 1, K, 2.0, 0, 1)
     with pytest.raises(hm.HmError):
         hm.muller_far_block_host(wl["bodies"], wl["ms"], 8, K, 2.0, 10 ** 6, 1)
+
+
+def _near_compare(name, eps, rule):
+    wl = workloads.workload(name)
+    o = oracle.MullerOracle(wl["bodies"], wl["ms"], wl["nc"], K, eps)
+    flags = o.near_flags()
+    nc2 = wl["nc"] ** 2
+    worst = 0.0
+    for tn in (0, 5, nc2 // 2 + 3, 2 * nc2 + 7):
+        q = tn // nc2
+        for p in np.flatnonzero(flags[q])[:4]:   # the self patch and its neighbours
+            ref = o.near_block(tn, p)
+            got = hm.muller_near_block_host(wl["bodies"], wl["ms"], wl["nc"], K, eps, tn, int(p), *rule)
+            worst = max(worst, np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    return worst
+
+
+@pytest.mark.parametrize("eps", [2.25, 10.0, 4.0 - 1.5j])
+@pytest.mark.parametrize("name", ["sphere_d2_m2_nc6", "ellipsoid_small", "sphere_d1_m1_nc8"])
+def test_near_rule_matches_the_oracle_integrals(name, eps):
+    # the device near-field rule (24/24/16 points, inner panel 0.5) against the oracle's
+    # independent adaptive + Duffy integrals of the same N-Mueller integrand
+    assert _near_compare(name, eps, (0, 0, 0, 0.0)) < 2e-9
+
+
+@pytest.mark.parametrize("name", ["sphere_d2_m2_nc6", "sphere_d1_m1_nc8"])
+def test_near_rule_at_high_contrast_needs_more_points(name):
+    # eps_r = 80: the interior wavelength is 1/9 of the exterior one; with the points
+    # doubled the rule meets the oracle again (the default rule does not: 3e-5 to 3e-3)
+    assert _near_compare(name, 80.0, (48, 48, 32, 0.0)) < 1e-8
