@@ -261,12 +261,13 @@ void hm_destroy(hm_handle h);
  * balanced median bisection along the widest bounding-box axis, leaf clusters of at
  * most `leaf` unknowns; admissibility of Eq. 21, min(diam) <= eta dist of the
  * bounding boxes, dist > 0), computed on the host from node positions xyz [nnode][3]
- * (two unknowns per node, interleaved).  *nblocks receives the number of leaves;
+ * with dof unknowns per node kept together and interleaved (2: the MFIE's J^u, J^v;
+ * 4: the N-Mueller system's J^u, J^v, M^u, M^v).  *nblocks receives the number of leaves;
  * blocks (may be NULL) receives [nblocks][5] = type (0 dense, 1 admissible), row0,
  * nrow, col0, ncol in tree-ordered unknowns; perm_node (may be NULL) [nnode] receives
  * the natural node at each tree position.  Blocks are those before ACA, which may
  * split an admissible block further. */
-hm_status hm_plan_host(const double *xyz, int nnode, int leaf, double eta, int *nblocks, int *blocks,
+hm_status hm_plan_host(const double *xyz, int nnode, int dof, int leaf, double eta, int *nblocks, int *blocks,
                        int *perm_node);
 
 /* N-Mueller formulation of a dielectric body (Sec. II.A, Eqs. 7-9 with

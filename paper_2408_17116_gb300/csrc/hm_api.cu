@@ -445,10 +445,10 @@ hm_status hm_fill(hm_handle h)
                                 const Cluster &t2 = h->clusters[ct.child[a]], &s2 = h->clusters[cs.child[c]];
                                 ch->t = ct.child[a];
                                 ch->s = cs.child[c];
-                                ch->r0 = 2 * t2.off;
-                                ch->nr = 2 * t2.cnt;
-                                ch->c0 = 2 * s2.off;
-                                ch->nc = 2 * s2.cnt;
+                                ch->r0 = h->dof * t2.off;
+                                ch->nr = h->dof * t2.cnt;
+                                ch->c0 = h->dof * s2.off;
+                                ch->nc = h->dof * s2.cnt;
                                 ch->type = B_LR;
                                 b->ch[2 * a + c] = ch;
                                 next.push_back(ch);

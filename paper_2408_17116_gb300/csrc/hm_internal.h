@@ -85,6 +85,7 @@ struct hm_handle_s {
     NearRule rule{24, 24, 16, 0.5};
     // geometry
     int nc = 0, nbodies = 0, npatch = 0, nnode = 0, N = 0;
+    int dof = 2;  // unknowns per node, kept together and interleaved (2: J^u, J^v)
     std::vector<DevBody> bodies;
     std::vector<DevPatch> patches;
     DevBody *d_bodies = nullptr;

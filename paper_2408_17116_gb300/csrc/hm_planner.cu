@@ -127,10 +127,10 @@ static Block *build_blocks(hm_handle_s *h, int t, int s)
     h->blocks.push_back(b);
     b->t = t;
     b->s = s;
-    b->r0 = 2 * ct.off;
-    b->nr = 2 * ct.cnt;
-    b->c0 = 2 * cs.off;
-    b->nc = 2 * cs.cnt;
+    b->r0 = h->dof * ct.off;
+    b->nr = h->dof * ct.cnt;
+    b->c0 = h->dof * cs.off;
+    b->nc = h->dof * cs.cnt;
     double dist = bbox_dist(ct.bmin, ct.bmax, cs.bmin, cs.bmax);
     double dm = std::min(bbox_diam(ct.bmin, ct.bmax), bbox_diam(cs.bmin, cs.bmax));
     bool adm = dist > 0.0 && dm <= h->prm.eta * dist;
@@ -224,9 +224,9 @@ void plan_geometry(hm_handle_s *h)
     build_cluster_tree(h);
     std::vector<int> perm(h->N), iperm(h->N);
     for (int pos = 0; pos < h->nnode; ++pos)
-        for (int c = 0; c < 2; ++c) {
-            perm[2 * pos + c] = 2 * h->perm_node[pos] + c;
-            iperm[2 * h->perm_node[pos] + c] = 2 * pos + c;
+        for (int c = 0; c < h->dof; ++c) {
+            perm[h->dof * pos + c] = h->dof * h->perm_node[pos] + c;
+            iperm[h->dof * h->perm_node[pos] + c] = h->dof * pos + c;
         }
     h->d_perm = (int *)dalloc(h, sizeof(int) * h->N);
     h->d_iperm = (int *)dalloc(h, sizeof(int) * h->N);
@@ -239,11 +239,11 @@ void plan_geometry(hm_handle_s *h)
 
 // Cluster tree over the host node table: balanced median bisection along the widest
 // bounding-box axis to a common leaf depth (the first depth whose clusters hold at
-// most n_leaf unknowns, two per node).
+// most n_leaf unknowns, dof per node).
 void build_cluster_tree(hm_handle_s *h)
 {
     int depth = 0;
-    while (2 * ((h->nnode + (1 << depth) - 1) >> depth) > h->prm.leaf && (1 << depth) < h->nnode) ++depth;
+    while (h->dof * ((h->nnode + (1 << depth) - 1) >> depth) > h->prm.leaf && (1 << depth) < h->nnode) ++depth;
     h->perm_node.resize(h->nnode);
     std::iota(h->perm_node.begin(), h->perm_node.end(), 0);
     h->clusters.clear();
@@ -251,14 +251,15 @@ void build_cluster_tree(hm_handle_s *h)
     build_clusters(h, 0, h->nnode, 0, depth, root);
 }
 
-extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int leaf, double eta, int *nblocks, int *blocks,
-                                  int *perm_node)
+extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int leaf, double eta, int *nblocks,
+                                  int *blocks, int *perm_node)
 {
-    if (!xyz || nnode <= 0 || leaf < 2 || !(eta > 0.0) || !nblocks) return HM_ERR_ARG;
+    if (!xyz || nnode <= 0 || (dof != 2 && dof != 4) || leaf < dof || !(eta > 0.0) || !nblocks) return HM_ERR_ARG;
     try {
         hm_handle_s h;  // host-only planning: no stream, no device memory
         h.nnode = nnode;
-        h.N = 2 * nnode;
+        h.dof = dof;
+        h.N = dof * nnode;
         h.prm.leaf = leaf;
         h.prm.eta = eta;
         h.h_nodes.assign(14 * (size_t)nnode, 0.0);

@@ -76,7 +76,7 @@ def load(path=SO):
     L.hm_farfield.argtypes = [P, I, P, I, P, P, P]
     L.hm_matvec.argtypes = [P, I, P, P]
     L.hm_farfield_static.argtypes = [P, I, P, I, P, P, P]
-    L.hm_plan_host.argtypes = [P, I, I, D, ctypes.POINTER(I), P, P]
+    L.hm_plan_host.argtypes = [P, I, I, I, D, ctypes.POINTER(I), P, P]
     L.hm_muller_far_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, P]
     L.hm_muller_near_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, I, I, I, D, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
@@ -113,18 +113,18 @@ def _np_ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def plan_host(xyz, leaf, eta):
+def plan_host(xyz, leaf, eta, dof=2):
     """Block cluster tree of hm_plan_host (host only): (blocks [n][5], perm_node [nnode])."""
     L = load()
     xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
     n = ctypes.c_int()
-    st = L.hm_plan_host(_np_ptr(xyz), xyz.shape[0], int(leaf), float(eta), ctypes.byref(n), None, None)
+    st = L.hm_plan_host(_np_ptr(xyz), xyz.shape[0], int(dof), int(leaf), float(eta), ctypes.byref(n), None, None)
     if st != HM_OK:
         raise HmError(st, "hm_plan_host")
     blocks = np.empty((n.value, 5), dtype=np.int32)
     perm = np.empty(xyz.shape[0], dtype=np.int32)
-    st = L.hm_plan_host(_np_ptr(xyz), xyz.shape[0], int(leaf), float(eta), ctypes.byref(n), _np_ptr(blocks),
-                        _np_ptr(perm))
+    st = L.hm_plan_host(_np_ptr(xyz), xyz.shape[0], int(dof), int(leaf), float(eta), ctypes.byref(n),
+                        _np_ptr(blocks), _np_ptr(perm))
     if st != HM_OK:
         raise HmError(st, "hm_plan_host")
     return blocks, perm

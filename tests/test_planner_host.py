@@ -26,24 +26,25 @@ def _dist_diam(p1, p2):
     return np.linalg.norm(gap), min(np.linalg.norm(a1 - a0), np.linalg.norm(b1 - b0))
 
 
+@pytest.mark.parametrize("dof", [2, 4])
 @pytest.mark.parametrize("name", ["sphere_d2_m2_nc6", "ellipsoid_small", "sphere_d4_m2_nc10"])
-def test_block_tree_invariants(name):
+def test_block_tree_invariants(name, dof):
     xyz, wl = _geometry(name)
     leaf, eta = wl["leaf"], wl["eta"]
-    blocks, perm = hm.plan_host(xyz, leaf, eta)
+    blocks, perm = hm.plan_host(xyz, leaf, eta, dof)
     n = xyz.shape[0]
-    N = 2 * n
+    N = dof * n
     assert np.array_equal(np.sort(perm), np.arange(n))
     # exact tiling of the N x N matrix
     cover = np.zeros((N, N), dtype=np.int16)
     for typ, r0, nr, c0, nc in blocks:
-        assert r0 % 2 == 0 and nr % 2 == 0 and c0 % 2 == 0 and nc % 2 == 0  # nodes stay whole
+        assert r0 % dof == 0 and nr % dof == 0 and c0 % dof == 0 and nc % dof == 0  # nodes stay whole
         cover[r0:r0 + nr, c0:c0 + nc] += 1
     assert (cover == 1).all()
     pts = xyz[perm]
     sizes = set()
     for typ, r0, nr, c0, nc in blocks:
-        pr, pc = pts[r0 // 2:(r0 + nr) // 2], pts[c0 // 2:(c0 + nc) // 2]
+        pr, pc = pts[r0 // dof:(r0 + nr) // dof], pts[c0 // dof:(c0 + nc) // dof]
         dist, dmin = _dist_diam(pr, pc)
         if typ == 1:
             assert dist > 0 and dmin <= eta * dist * (1 + 1e-12)
@@ -51,7 +52,7 @@ def test_block_tree_invariants(name):
             assert not (dist > 0 and dmin <= eta * dist * (1 - 1e-12))
             assert nr <= leaf and nc <= leaf
             sizes.update((nr, nc))
-    assert max(sizes) - min(sizes) <= 2  # balanced bisection: leaf clusters differ by one node at most
+    assert max(sizes) - min(sizes) <= dof  # balanced bisection: leaf clusters differ by one node at most
     assert (blocks[:, 0] == 1).sum() > 0
 
 
@@ -66,6 +67,8 @@ def test_rejects_bad_arguments():
         hm.plan_host(np.zeros((0, 3)), 64, 2.0)
     with pytest.raises(hm.HmError):
         hm.plan_host(np.random.default_rng(0).random((10, 3)), 1, 2.0)
+    with pytest.raises(hm.HmError):
+        hm.plan_host(np.random.default_rng(0).random((10, 3)), 16, 2.0, dof=3)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 33])
