@@ -289,6 +289,14 @@ hm_status hm_muller_far_block_host(const hm_body *bodies, int nbodies, int nodes
 hm_status hm_muller_near_block_host(const hm_body *bodies, int nbodies, int nodes_per_dir, double k0,
                                     double eps_re, double eps_im, int tn, int p, int qd, int qi, int qo, double t0,
                                     void *out);
+/* N-Mueller right-hand side and far field on the host: rhs_out (may be NULL) receives
+ * complex128 [4 nnode] for the plane wave E = pol exp(-jk khat.r) (khat, pol: [3]),
+ * rows (E-u, E-v, H-u, H-v) per node = (t_b.E_inc, t_b.(khat x pol) exp(-jk khat.r));
+ * efar_out (may be NULL) receives complex128 [nang][3] = -jk/(4 pi) [(I - r r) N_J - r x N_M]
+ * for the solution x [4 nnode] (eta0 J^u, eta0 J^v, M^u, M^v per node). */
+hm_status hm_muller_rhs_farfield_host(const hm_body *bodies, int nbodies, int nodes_per_dir, double k0,
+                                      const double *khat, const double *pol, void *rhs_out, const void *x,
+                                      int nang, const double *obs, void *efar_out);
 
 /* ---- inspection (tests and diagnostics; all synchronise) ------------------- */
 

@@ -260,3 +260,49 @@ __host__ __device__ inline int near_axis_points(const NearAxis &ax, const double
     }
     return n;
 }
+
+// ---------------------------------------------------------------------------
+// Right-hand side of one node for the plane wave E = pol exp(-jk khat.r):
+// E-row b: t_b . E_inc, H-row b: t_b . (eta0 H_inc) = t_b . (khat x pol) exp(-jk khat.r).
+// X: node table SoA [14][nnode].  out[4]: (E-u, E-v, H-u, H-v).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void muller_rhs_node(const double *X, int nnode, int i, double k, const double *kh,
+                                                const double *po, zc *out)
+{
+    const int n = nnode;
+    double h0[3] = {kh[1] * po[2] - kh[2] * po[1], kh[2] * po[0] - kh[0] * po[2], kh[0] * po[1] - kh[1] * po[0]};
+    double ph = -k * (kh[0] * X[i] + kh[1] * X[n + i] + kh[2] * X[2 * n + i]);
+    zc e = zmake(cos(ph), sin(ph));
+    double au[3] = {X[3 * n + i], X[4 * n + i], X[5 * n + i]};
+    double av[3] = {X[6 * n + i], X[7 * n + i], X[8 * n + i]};
+    out[0] = zscale(e, -(av[0] * po[0] + av[1] * po[1] + av[2] * po[2]));
+    out[1] = zscale(e, au[0] * po[0] + au[1] * po[1] + au[2] * po[2]);
+    out[2] = zscale(e, -(av[0] * h0[0] + av[1] * h0[1] + av[2] * h0[2]));
+    out[3] = zscale(e, au[0] * h0[0] + au[1] * h0[1] + au[2] * h0[2]);
+}
+
+// Contribution of node j to the radiation vectors in direction rh:
+// NJ += w_j (Jbar^u a_u + Jbar^v a_v) exp(jk rh.r_j), NM likewise with M (x: 4 values).
+// The far field is E_far = -jk/(4 pi) [(I - rh rh) NJ - rh x NM].
+__host__ __device__ inline void muller_radiation_add(const double *X, int nnode, int j, double k, const double *rh,
+                                                     const zc *x, zc *NJ, zc *NM)
+{
+    const int n = nnode;
+    double ph = k * (rh[0] * X[j] + rh[1] * X[n + j] + rh[2] * X[2 * n + j]);
+    zc e = zscale(zmake(cos(ph), sin(ph)), X[13 * n + j]);
+    zc ju = zmul(x[0], e), jv = zmul(x[1], e), mu = zmul(x[2], e), mv = zmul(x[3], e);
+    for (int d = 0; d < 3; ++d) {
+        double au = X[(3 + d) * n + j], av = X[(6 + d) * n + j];
+        NJ[d] = zadd(NJ[d], zadd(zscale(ju, au), zscale(jv, av)));
+        NM[d] = zadd(NM[d], zadd(zscale(mu, au), zscale(mv, av)));
+    }
+}
+
+__host__ __device__ inline void muller_far_field(const double *rh, double k, const zc *NJ, const zc *NM, zc *E)
+{
+    zc rn = zadd(zadd(zscale(NJ[0], rh[0]), zscale(NJ[1], rh[1])), zscale(NJ[2], rh[2]));
+    zc rxm[3] = {zsub(zscale(NM[2], rh[1]), zscale(NM[1], rh[2])), zsub(zscale(NM[0], rh[2]), zscale(NM[2], rh[0])),
+                 zsub(zscale(NM[1], rh[0]), zscale(NM[0], rh[1]))};
+    zc pre = zmake(0.0, -k / (4.0 * 3.14159265358979323846));
+    for (int d = 0; d < 3; ++d) E[d] = zmul(pre, zsub(zsub(NJ[d], zscale(rn, rh[d])), rxm[d]));
+}

@@ -261,3 +261,36 @@ extern "C" hm_status hm_muller_far_block_host(const hm_body *bodies, int nbodies
         return HM_ERR_OOM;
     }
 }
+
+extern "C" hm_status hm_muller_rhs_farfield_host(const hm_body *bodies, int nbodies, int nodes_per_dir, double k0,
+                                                 const double *khat, const double *pol, void *rhs_out, const void *x,
+                                                 int nang, const double *obs, void *efar_out)
+{
+    if (!bodies || nbodies <= 0 || nodes_per_dir < 2 || nodes_per_dir > HM_NC_MAX || !(k0 > 0.0)) return HM_ERR_ARG;
+    try {
+        const int nc = nodes_per_dir;
+        std::vector<DevBody> B;
+        std::vector<DevPatch> P;
+        std::vector<double> x1d, X;
+        host_geometry(bodies, nbodies, nc, B, P, x1d, X);
+        const int nnode = (int)P.size() * nc * nc;
+        if (rhs_out && khat && pol) {
+            zc *o = (zc *)rhs_out;
+            for (int i = 0; i < nnode; ++i) muller_rhs_node(X.data(), nnode, i, k0, khat, pol, o + 4 * (size_t)i);
+        }
+        if (x && nang > 0 && obs && efar_out) {
+            const zc *xs = (const zc *)x;
+            zc *E = (zc *)efar_out;
+            for (int a = 0; a < nang; ++a) {
+                zc NJ[3] = {zmake(0, 0), zmake(0, 0), zmake(0, 0)}, NM[3] = {zmake(0, 0), zmake(0, 0), zmake(0, 0)};
+                for (int j = 0; j < nnode; ++j) muller_radiation_add(X.data(), nnode, j, k0, obs + 3 * a, xs + 4 * j, NJ, NM);
+                muller_far_field(obs + 3 * a, k0, NJ, NM, E + 3 * (size_t)a);
+            }
+        }
+        return HM_OK;
+    } catch (const HmError &e) {
+        return e.st;
+    } catch (...) {
+        return HM_ERR_OOM;
+    }
+}

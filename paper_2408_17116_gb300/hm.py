@@ -31,7 +31,8 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_get_perm_host", "hm_get_blocks_host", "hm_get_block_dense_host", "hm_rank_samples",
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
-           "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host")
+           "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host",
+           "hm_muller_rhs_farfield_host")
 
 
 class hm_params(ctypes.Structure):
@@ -79,6 +80,7 @@ def load(path=SO):
     L.hm_plan_host.argtypes = [P, I, I, I, D, ctypes.POINTER(I), P, P]
     L.hm_muller_far_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, P]
     L.hm_muller_near_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, I, I, I, D, P]
+    L.hm_muller_rhs_farfield_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, P, P, P, P, I, P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
@@ -154,6 +156,33 @@ def muller_near_block_host(bodies, ms, nc, k0, eps_r, tn, p, qd=0, qi=0, qo=0, t
     if st != HM_OK:
         raise HmError(st, "hm_muller_near_block_host")
     return out
+
+
+def muller_rhs_farfield_host(bodies, ms, nc, k0, khat=None, pol=None, x=None, dirs=None):
+    """N-Mueller right-hand side [4 nnode] and far field [nang][3] (host)."""
+    L = load()
+    arr = make_bodies(bodies, ms)
+    nnode = 6 * int(np.sum(np.asarray(ms) ** 2)) * int(nc) ** 2
+    rhs = efar = None
+    kp = pp = xp = dp = ep = None
+    if khat is not None:
+        kh = np.ascontiguousarray(np.asarray(khat, np.float64).reshape(3))
+        po = np.ascontiguousarray(np.asarray(pol, np.float64).reshape(3))
+        rhs = np.zeros(4 * nnode, dtype=np.complex128)
+        kp, pp, rp = _np_ptr(kh), _np_ptr(po), _np_ptr(rhs)
+    else:
+        rp = None
+    nang = 0
+    if x is not None:
+        xs = np.ascontiguousarray(np.asarray(x, np.complex128).reshape(-1))
+        d = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
+        nang = d.shape[0]
+        efar = np.zeros((nang, 3), dtype=np.complex128)
+        xp, dp, ep = _np_ptr(xs), _np_ptr(d), _np_ptr(efar)
+    st = L.hm_muller_rhs_farfield_host(arr, len(ms), int(nc), float(k0), kp, pp, rp, xp, nang, dp, ep)
+    if st != HM_OK:
+        raise HmError(st, "hm_muller_rhs_farfield_host")
+    return rhs, efar
 
 
 def make_bodies(bodies, ms):

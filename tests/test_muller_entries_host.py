@@ -67,3 +67,18 @@ def test_near_rule_at_high_contrast_needs_more_points(name):
     # eps_r = 80: the interior wavelength is 1/9 of the exterior one; with the points
     # doubled the rule meets the oracle again (the default rule does not: 3e-5 to 3e-3)
     assert _near_compare(name, 80.0, (48, 48, 32, 0.0)) < 1e-8
+
+
+def test_rhs_and_far_field_match_the_oracle():
+    wl = workloads.workload("ellipsoid_small")
+    o = oracle.MullerOracle(wl["bodies"], wl["ms"], wl["nc"], K, 3.0)
+    kh, po = workloads.incidence(1, workloads.SEED + 3)
+    rhs, _ = hm.muller_rhs_farfield_host(wl["bodies"], wl["ms"], wl["nc"], K, kh[0], po[0])
+    ref = o.rhs(kh, po)[0]
+    assert np.max(np.abs(rhs - ref)) <= 1e-13 * np.max(np.abs(ref))
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(o.N) + 1j * rng.standard_normal(o.N)
+    _, dirs = workloads.rcs_cuts(19)
+    _, ef = hm.muller_rhs_farfield_host(wl["bodies"], wl["ms"], wl["nc"], K, x=x, dirs=dirs)
+    efo, _ = o.farfield(x, dirs)
+    assert np.max(np.abs(ef - efo)) <= 1e-12 * np.max(np.abs(efo))
