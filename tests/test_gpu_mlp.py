@@ -96,7 +96,7 @@ def test_rank_model_trained_on_method_ranks_gains_over_plain_aca():
     L0, _ = m.loss_grad(Xd, td)
     L = m.train(Xd, td, 2000, 3e-3)
     # most samples are attempts that reached the same bound, so the targets vary little:
-    # the fit is judged by the loss it removed and, below, by what it gains in the fill
+    # the fit is assessed by the loss it removed and, below, by what it gains in the fill
     assert L < 0.01 * L0, (L, L0, float(np.var(t)))
     # a body the model has not seen (a 4-wavelength sphere): doomed attempts skipped,
     # buffers sized by the prediction, the same operator to within the ACA tolerance
