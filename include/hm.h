@@ -6,7 +6,7 @@
  * Equation Method".  The solver discretises the MFIE of a PEC body (Sec. II.A,
  * Eq. 10, second row) with the CBIE (Sec. II.B, Eqs. 11-20), compresses the
  * system as an H-matrix (Sec. III, Eq. 21, ACA), factors it by H-LU and solves
- * by H-forward/back substitution (Sec. III.A, Eqs. 23-28) on the "entire matrix"
+ * by H-forward/back substitution (Sec. III.A, Eqs. 23-28) on the entire-matrix
  * ordering (Sec. III.B).
  *
  * Conventions shared by every call

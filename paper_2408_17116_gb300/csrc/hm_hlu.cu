@@ -1,6 +1,6 @@
 // H-LU factorisation and H-solve (Sec. III and III.A: block LU of Eq. 23 applied
 // recursively, forward substitution Eqs. 24, 26, 27, back substitution Eqs. 25,
-// 28), on the "entire matrix" block cluster tree (Sec. III.B).
+// 28), on the entire-matrix block cluster tree (Sec. III.B: one tree over all unknowns).
 //
 // Recursion on a diagonal block A = [[A11, A12], [A21, A22]]:
 //   A11 = P1^T L11 U11                       (recursive; partial pivoting inside dense leaves)
