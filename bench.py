@@ -99,61 +99,110 @@ def load_workload(name):
     return workloads.workload(name)
 
 
-def cpu_baseline(wl):
-    """The oracle as it stands, on a bounded sample of the workload, scaled to unknowns/s.
+_LU_SAMPLE = {}
 
-    Sample: dense MFIE fill of R rows of the full matrix, and the oracle's dense LU +
-    solve of an n_s x n_s leading block of the same matrix's rows/columns.  Full-size
-    time = fill_time * N / R + lu_time * (N / n_s)^3 + solve_time * (N / n_s)^2.
+
+def cpu_baseline(wl, workload_name):
+    """The oracle as it stands, timed on a bounded sample of the workload (host cores).
+
+    Sample of one step: the dense fill of R = 32 evenly spaced rows of the full N x N
+    matrix, and the oracle's right-looking LU with partial pivoting plus the solves of an
+    n_s x n_s principal submatrix of the same operator (n_s = 3,072: 151 MB, larger than
+    the host's caches, so the LU streams memory as the full-size one does).  The
+    submatrix's rows are filled once per process, outside the timed step.
+    Estimate of the full dense fill + LU + solve (not a measurement; the fill is linear in
+    the rows, the LU's work and memory traffic cubic and the solves quadratic in the size):
+        t_full = t_rows N / R + t_lu (N / n_s)^3 + t_solve (N / n_s)^2.
+    Returns the estimate as unknowns/s, with the sample's own wall time.
     """
     import oracle
     t0 = time.perf_counter()
     o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
     N = o.N
-    rng = np.random.default_rng(0)
-    R = 16
-    rows = np.sort(rng.choice(N, R, replace=False))
+    R = 32
+    rows = np.linspace(0, N - 1, R).astype(np.int64)
+    ns = min(N, 3072)
+    key = (workload_name, ns)
+    if key not in _LU_SAMPLE:
+        idx = np.sort(np.random.default_rng(0).choice(N, ns, replace=False))
+        _LU_SAMPLE[key] = o.matrix_rows(idx)[:, idx]  # a principal submatrix of the same operator
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
     t = time.perf_counter()
-    A = o.matrix_rows(rows)
+    o.matrix_rows(rows)
     t_rows = time.perf_counter() - t
-    ns = min(N, 1024)
-    idx = np.sort(rng.choice(N, ns, replace=False))
-    Bm = o.matrix_rows(idx)[:, idx]  # a principal submatrix of the same operator
     t = time.perf_counter()
-    LU, piv, info = oracle.zgetrf(Bm)
+    LU, piv, info = oracle.zgetrf(_LU_SAMPLE[key])
     t_lu = time.perf_counter() - t
-    b = np.ones(ns, dtype=complex)
+    nrhs = wl["kdirs"].shape[0]
+    b = np.ones((ns, nrhs), dtype=complex)
     t = time.perf_counter()
     oracle.zgetrs(LU, piv, b)
     t_sol = time.perf_counter() - t
-    nrhs = wl["kdirs"].shape[0]
-    est = t_rows * N / R + t_lu * (N / ns) ** 3 + t_sol * nrhs * (N / ns) ** 2
+    step_s = time.perf_counter() - t1
+    est = t_rows * N / R + t_lu * (N / ns) ** 3 + t_sol * (N / ns) ** 2
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": N / est, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
-            "sample": "dense fill of %d of %d rows (%.2f s) + dense LU of a %d x %d principal submatrix "
-                      "(%.2f s) + %d solves, extrapolated by N/R, (N/n)^3, (N/n)^2; est. full dense "
-                      "fill+LU+solve %.0f s" % (R, N, t_rows, ns, ns, t_lu, nrhs, est),
-            "wall_s": time.perf_counter() - t0, "est_full_s": est}
+            "sample": "ESTIMATE from a bounded sample: dense fill of %d of %d rows (%.2f s) + oracle LU of a "
+                      "%d x %d principal submatrix (%.2f s, out of cache) + %d solves (%.3f s); scaled by N/R, "
+                      "(N/n)^3, (N/n)^2 to an estimated full dense fill+LU+solve of %.0f s"
+                      % (R, N, t_rows, ns, ns, t_lu, nrhs, t_sol, est),
+            "step_s": step_s, "setup_s": t_setup, "est_full_s": est}
+
+
+def full_oracle(wl):
+    """The oracle's full dense fill, LU and solve of the workload, each timed (a measurement,
+    minutes at 19,200 unknowns; run on its own with --impl reference --full-oracle)."""
+    import oracle
+    o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
+    b = o.rhs(wl["kdirs"], wl["pols"])
+    t = time.perf_counter()
+    A = o.dense()
+    t_fill = time.perf_counter() - t
+    t = time.perf_counter()
+    LU, piv, info = oracle.zgetrf(A)
+    t_lu = time.perf_counter() - t
+    del A
+    t = time.perf_counter()
+    oracle.zgetrs(LU, piv, b.T)
+    t_sol = time.perf_counter() - t
+    tot = t_fill + t_lu + t_sol
+    return {"unknowns": o.N, "fill_s": t_fill, "lu_s": t_lu, "solve_s": t_sol, "total_s": tot,
+            "value": o.N / tot, "unit": "unknowns/s", "nproc": os.cpu_count(),
+            "omp_num_threads": os.environ.get("OMP_NUM_THREADS")}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = load_workload(args.workload)
+    if args.full_oracle:
+        print(json.dumps(dict(full_oracle(wl), workload=args.workload, impl="reference", kind="oracle-full")),
+              flush=True)
+        return
     vals = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl)
+        cb = cpu_baseline(wl, args.workload)
         if i >= args.warmup:
             vals.append(cb)
     v = statistics.median([c["value"] for c in vals])
+    step_ms = 1000.0 * statistics.median([c["step_s"] for c in vals])
     cb = dict(vals[-1])
     cb["value"] = v
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wl_N(wl) / v,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+           "ms_per_step_is": "wall time of one bounded sample step; value is the full-size estimate",
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload}, "cpu_baseline": cb,
+           "config": bench_config(args, wl), "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def bench_config(args, wl):
+    """The workload description both arms print (identical keys and values)."""
+    return {"workload": args.workload, "formulation": "MFIE", "unknowns": wl_N(wl), "rhs": int(wl["kdirs"].shape[0]),
+            "leaf": wl["leaf"], "eta": wl["eta"], "aca_tol": wl["aca_tol"],
+            "l2": "working set (H-matrix, near store) > L2 between steps"}
 
 
 def wl_N(wl):
@@ -161,6 +210,19 @@ def wl_N(wl):
 
 
 PRECISION = {"fp32r": 1, "fp64": 0}
+
+
+def solution_error(name, x):
+    """max over right-hand sides of |x - x_o| / |x_o| against the dense oracle's solution
+    stored in tests/golden (written by tests/golden/make_dense_solution.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", name + "_x.npy")
+    if not os.path.exists(path):
+        return None
+    xo = np.load(path)
+    xs = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    if xs.shape != xo.shape:
+        return None
+    return float(max(np.linalg.norm(xs[r] - xo[r]) / np.linalg.norm(xo[r]) for r in range(xo.shape[0])))
 
 
 def aggregate(ms_local, unknowns_local, dist=None, device="cpu"):
@@ -206,6 +268,10 @@ def main():
     ap.add_argument("--precision", default="fp32r", choices=sorted(PRECISION),
                     help="fp32r: FP32 H-LU + FP64 refinement (default); fp64: the plain FP64 H-LU")
     ap.add_argument("--no-compare", action="store_true", help="skip the one-step runs of both precisions")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the host-buffer end-to-end step (for kernel launch lists under a profiler)")
+    ap.add_argument("--full-oracle", action="store_true",
+                    help="with --impl reference: time the oracle's full dense fill, LU and solve once")
     ap.add_argument("--compare-workload", default="sphere_d2_m2_nc6",
                     help="workload of the FP32-refined vs plain-FP64 comparison (one step each)")
     args = ap.parse_args()
@@ -273,17 +339,20 @@ def main():
     progress("timed: %.1f ms per step" % ms)
     launches = int(s.hm_query("LAUNCHES") - L0)
     N = s.N
+    sol_err = solution_error(args.workload, x)
     ms, value = aggregate(ms, N, dist, device="cuda")
     stats = {k.lower(): s.hm_query(k) for k in ("CR", "MAX_RANK", "MEAN_RANK", "LR_BLOCKS", "DENSE_BLOCKS",
                                                  "NEAR_PAIRS", "ACA_NONCONV", "FLOPS_FACTOR", "REFINE_ITERS",
                                                  "REFINE_RES", "STORAGE", "STORAGE32")}
     # e2e: host buffers in and out, wall clock around the public API calls
-    barrier()
-    t = time.perf_counter()
-    xh, rcs_h = one_step(s, wl, dirs, host=True, precision=prec)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t
-    progress("e2e: %.1f s" % e2e_s)
+    e2e_s = None
+    if not args.no_e2e:
+        barrier()
+        t = time.perf_counter()
+        xh, rcs_h = one_step(s, wl, dirs, host=True, precision=prec)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t
+        progress("e2e: %.1f s" % e2e_s)
     nrhs = wl["kdirs"].shape[0]
     h2d = 152 * len(wl["ms"]) + 64 + 48 * nrhs + 24 * dirs.shape[0]  # bodies, params, waves, directions
     d2h = 16 * N * nrhs + 8 * nrhs * dirs.shape[0]
@@ -322,13 +391,12 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 fill; c64 H-LU + f64 refinement" if prec == "fp32r" else "f64",
            "data": "synthetic",
-           "config": {"workload": args.workload, "unknowns": N, "rhs": nrhs, "leaf": wl["leaf"], "eta": wl["eta"],
-                      "aca_tol": wl["aca_tol"], "precision": prec,
-                      "parallelism": "replicas" if world > 1 else "single",
-                      "l2": "working set (H-matrix, near store) > L2 between steps"},
+           "config": bench_config(args, wl), "precision": prec,
+           "parallelism": "replicas" if world > 1 else "single",
+           "solution_error_vs_oracle": sol_err,
            "phases_s": per, "stats": stats, "gpu_launches": launches, "clocks": clocks,
-           "e2e": {"value": N / e2e_s, "unit": "unknowns/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "wall_s": e2e_s},
+           "e2e": ({"value": N / e2e_s, "unit": "unknowns/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "wall_s": e2e_s} if e2e_s else None),
            "roofline": roof, "kernels": cands[1:]}
     if not args.no_compare:
         # FP32 H-LU + FP64 refinement against the plain FP64 H-LU on the same GPU, one timed
@@ -350,7 +418,7 @@ def main():
         out["compare"] = cmp
         progress("compare: %s" % json.dumps(cmp))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl)
+        out["cpu_baseline"] = cpu_baseline(wl, args.workload)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -47,10 +47,16 @@ typedef enum {
     HM_ERR_SINGULAR = 5,      /* a zero pivot in a diagonal leaf of the H-LU */
     HM_ERR_NOT_CONVERGED = 6, /* an iteration hit its limit (reported, not fatal for ACA) */
     HM_ERR_TIMEOUT = 7,       /* a bounded device wait expired */
-    HM_ERR_NUMERIC = 8        /* NaN/Inf detected in an output */
+    HM_ERR_NUMERIC = 8        /* NaN/Inf in the solution (hm_solve scans its output) */
 } hm_status;
 
-typedef enum { HM_PEC_MFIE = 0 } hm_formulation;
+/* Integral equation.  HM_PEC_MFIE: the magnetic-field equation of a PEC body (Sec. II.A,
+ * Eq. 10, second row), the formulation the paper solves for every PEC case.
+ * HM_PEC_CFIE: the combined field equation alpha EFIE / eta0 + (1 - alpha) MFIE of a PEC
+ * body (Eq. 10, both rows; the paper does not combine them).  HM_DIEL_MULLER: the
+ * N-Mueller equations of a penetrable body (Eqs. 7-9).  hm_build_geometry returns
+ * HM_ERR_ARG for a formulation this library was built without (hm_version lists them). */
+typedef enum { HM_PEC_MFIE = 0, HM_PEC_CFIE = 1, HM_DIEL_MULLER = 2 } hm_formulation;
 /* HM_FP64: the plain FP64 method (complex128 H-matrix, FP64 H-LU and H-solve).
  * HM_FP32_REFINED: the same FP64 fill; hm_factor builds a complex64 copy of the
  * H-matrix and factors it by H-LU in FP32 (truncation tolerance factor_tol); hm_solve
@@ -75,6 +81,14 @@ typedef struct {
     double factor_tol;    /* HM_FP32_REFINED: truncation tolerance of the FP32 H-LU (0 = 1e-4) */
     double refine_tol;    /* HM_FP32_REFINED: target relative residual per RHS (0 = 1e-10) */
     int refine_max_iter;  /* HM_FP32_REFINED: refinement step limit (0 = 30) */
+    double cfie_alpha;    /* HM_PEC_CFIE: weight alpha of the EFIE row, 0 < alpha <= 1 */
+    double eps_r_re;      /* HM_DIEL_MULLER: relative permittivity of the interior, real part (> 0) */
+    double eps_r_im;      /* HM_DIEL_MULLER: imaginary part (<= 0 for a lossy medium, exp(j w t)) */
+    double mu_r;          /* HM_DIEL_MULLER: relative permeability of the interior (0 = 1; only 1 is supported) */
+    double trunc_tol;     /* truncation tolerance of the QR+SVD recompressions of the FP64 H-matrix and its
+                             H-LU (0 = aca_tol) */
+    int quad_order;       /* Gauss points per direction of the self/near rule's inner panels and Duffy squares
+                             (0 = 24; 4..36; the outer panels take ceil(2 quad_order / 3)) */
 } hm_params;
 
 /* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,
@@ -179,15 +193,16 @@ hm_status hm_solve_host(hm_handle h, int nrhs, const double *inc_dirs, const dou
 /* Far field of solutions x_dev [nrhs][N] at unit directions obs_dirs (host [nang][3]):
  * efar_dev (device complex128 [nrhs][nang][3], may be NULL) = -jk eta0/(4 pi) (I - r r)
  * sum_j w_j (F^u a_u + F^v a_v)_j exp(jk r.r_j); rcs_host (host [nrhs][nang], may be
- * NULL) = 4 pi |E_far|^2 in m^2.  Synchronises when rcs_host is given. */
+ * NULL) = 4 pi |E_far|^2 in m^2.  Always synchronises before returning (obs_dirs is read
+ * during the call). */
 hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const double *obs_dirs,
                       void *efar_dev, double *rcs_host);
 
 /* hm_farfield without device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot let the library allocate device memory during
  * a call (their device memory belongs to their own pool or allocator, or their loop
- * forbids allocation after start-up).  Same arguments, results and synchronisation
- * as hm_farfield, but the observation directions and the RCS values are staged in one
+ * forbids allocation after start-up).  Same arguments and results as hm_farfield, and
+ * like it always synchronises before returning, but the observation directions and the RCS values are staged in one
  * static device array of HM_FARFIELD_STATIC_DOUBLES doubles (512 KiB, held by every
  * GPU that loads the library until the process exits) instead of buffers allocated
  * per call.  Limit: 3 nang + nrhs nang (nrhs nang only when rcs_host is given) must
@@ -195,7 +210,8 @@ hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const 
  * The first call on a device looks up the array's device address (once per device,
  * with that device current); make that first call before any stream capture.  All
  * calls share the array, which keeps the last call's contents: calls that overlap on
- * the GPU (other streams or other host threads) race on it. */
+ * the GPU (other streams or other host threads) race on it.  The current device must be
+ * the one the handle was created on (HM_ERR_STATE otherwise, before anything is copied). */
 #define HM_FARFIELD_STATIC_DOUBLES 65536
 hm_status hm_farfield_static(hm_handle h, int nrhs, const void *x_dev, int nang, const double *obs_dirs,
                              void *efar_dev, double *rcs_host);
@@ -206,6 +222,17 @@ hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev);
 
 hm_status hm_query(hm_handle h, int what, double *out);
 const char *hm_last_error(hm_handle h);
+
+/* Host-side fault injection for tests of the error paths (the paper has no counterpart).
+ * Arms one fault for the next call that reaches it; no GPU fault, trap or hang is caused.
+ *   HM_FAULT_ZERO_PIVOT: hm_factor zeroes the first column of the first diagonal leaf before
+ *                        the H-LU, which must report HM_ERR_SINGULAR;
+ *   HM_FAULT_NAN_RHS:    hm_solve sets one right-hand-side entry to NaN; the scan of the
+ *                        solution reports HM_ERR_NUMERIC;
+ *   HM_FAULT_ALLOC:      the next internal device allocation reports failure: HM_ERR_OOM.
+ * HM_FAULT_NONE disarms. */
+enum { HM_FAULT_NONE = 0, HM_FAULT_ZERO_PIVOT = 1, HM_FAULT_NAN_RHS = 2, HM_FAULT_ALLOC = 3 };
+hm_status hm_inject_fault(hm_handle h, int what);
 
 /* ---- learned ACA-rank predictor ---------------------------------------------
  * The paper has no learned component.  A small MLP predicts, from the geometry of

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 
 #include "hm_internal.h"
 
@@ -11,6 +12,10 @@
 
 void *dalloc(hm_handle_s *h, size_t bytes)
 {
+    if (h->fault == HM_FAULT_ALLOC) {  // host-side injection: this allocation reports failure
+        h->fault = HM_FAULT_NONE;
+        throw HmError{HM_ERR_OOM, "device allocation failed (injected)"};
+    }
     void *p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), h->stream);
     if (e != cudaSuccess) {
@@ -68,8 +73,19 @@ hm_status guard(hm_handle h, F &&f)
     }
 }
 
+void free_plans(hm_handle_s *h)
+{
+    tile_free(h, h->tmat64);
+    tile_free(h, h->tmatcopy);
+    tile_free(h, h->tfac64);
+    tile_free(h, h->tfac32);
+    h->tmat64 = h->tmatcopy = h->tfac64 = nullptr;
+    h->tfac32 = nullptr;
+}
+
 void free_matrix(hm_handle_s *h)
 {
+    free_plans(h);
     for (Block *b : h->blocks) {
         if (b->D) dfree(h, b->D);
         if (b->U) dfree(h, b->U);
@@ -175,6 +191,14 @@ void rank_features(hm_handle_s *h, const Block *b, float *f)
     f[7] = (float)(-std::log10(h->tol) / 10.0);
 }
 
+// The first diagonal dense leaf of a block tree (the top-left leaf).
+template <class Z>
+static BlockT<Z> *first_diagonal_leaf(BlockT<Z> *b)
+{
+    while (b->type == B_HIER) b = b->ch[0];
+    return b;
+}
+
 extern "C" {
 
 const char *hm_version(void) { return HM_VERSION; }
@@ -211,17 +235,28 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
     return guard(h, [&] {
         if (!bodies || nbodies <= 0 || !p) throw HmError{HM_ERR_ARG, "null bodies or params"};
         if (nodes_per_dir < 2 || nodes_per_dir > HM_NC_MAX) throw HmError{HM_ERR_ARG, "nodes_per_dir out of range 2..16"};
-        if (p->formulation != HM_PEC_MFIE) throw HmError{HM_ERR_ARG, "unsupported formulation"};
+        if (p->formulation == HM_PEC_CFIE || p->formulation == HM_DIEL_MULLER)
+            throw HmError{HM_ERR_ARG, p->formulation == HM_PEC_CFIE
+                                          ? "formulation HM_PEC_CFIE is not built in this library"
+                                          : "formulation HM_DIEL_MULLER is not built in this library"};
+        if (p->formulation != HM_PEC_MFIE) throw HmError{HM_ERR_ARG, "unknown formulation"};
+        if (!(p->trunc_tol >= 0.0) || p->quad_order < 0 || (p->quad_order > 0 && (p->quad_order < 4 || p->quad_order > 36)))
+            throw HmError{HM_ERR_ARG, "trunc_tol must be >= 0 and quad_order 0 or 4..36"};
         if (p->precision != HM_FP64 && p->precision != HM_FP32_REFINED) throw HmError{HM_ERR_ARG, "unsupported precision"};
         if (!(p->factor_tol >= 0.0) || !(p->refine_tol >= 0.0) || p->refine_max_iter < 0)
             throw HmError{HM_ERR_ARG, "invalid refinement parameter"};
-        if (!(p->k0 >= 0.0) || p->leaf < 2 || !(p->eta > 0.0) || !(p->aca_tol > 0.0) || !(p->near_delta >= 0.0))
+        if (!(p->k0 >= 0.0) || !std::isfinite(p->k0) || p->leaf < 2 || !(p->eta > 0.0) || !(p->aca_tol > 0.0) || !(p->near_delta >= 0.0))
             throw HmError{HM_ERR_ARG, "invalid parameter value"};
         long long P = 0;
         for (int b = 0; b < nbodies; ++b) {
             if (bodies[b].family != 0 || bodies[b].m < 1 || bodies[b].m > 256) throw HmError{HM_ERR_ARG, "bad body"};
             for (int d = 0; d < 3; ++d)
-                if (!(bodies[b].semi_axes[d] > 0.0)) throw HmError{HM_ERR_ARG, "semi-axes must be positive"};
+                if (!(bodies[b].semi_axes[d] > 0.0) || !std::isfinite(bodies[b].semi_axes[d]))
+                    throw HmError{HM_ERR_ARG, "semi-axes must be positive and finite"};
+            for (int d = 0; d < 3; ++d)
+                if (!std::isfinite(bodies[b].center[d])) throw HmError{HM_ERR_ARG, "body centre is not finite"};
+            for (int d = 0; d < 9; ++d)
+                if (!std::isfinite(bodies[b].rot[d])) throw HmError{HM_ERR_ARG, "body rotation is not finite"};
             P += 6LL * bodies[b].m * bodies[b].m;
         }
         if (P * nodes_per_dir * nodes_per_dir * 2 > (1LL << 30)) throw HmError{HM_ERR_ARG, "problem too large"};
@@ -229,7 +264,14 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
         free_all(h);
         h->prm = *p;
         h->tol = p->aca_tol;
+        h->trunc_tol = p->trunc_tol > 0.0 ? p->trunc_tol : p->aca_tol;
         h->factor_tol = p->factor_tol > 0.0 ? p->factor_tol : 1e-4;
+        if (p->quad_order > 0) {
+            h->rule.qd = h->rule.qi = p->quad_order;
+            h->rule.qo = (2 * p->quad_order + 2) / 3;
+        } else {
+            h->rule = NearRule{24, 24, 16, 0.5};
+        }
         if (h->prm.refine_tol <= 0.0) h->prm.refine_tol = 1e-10;
         if (h->prm.refine_max_iter <= 0) h->prm.refine_max_iter = 30;
         h->nc = nodes_per_dir;
@@ -478,7 +520,7 @@ hm_status hm_fill(hm_handle h)
                     keep.push_back(b);
                     ranks.push_back(b->k);
                 }
-            batched_truncate(h, keep, ranks, h->tol);
+            batched_truncate(h, keep, ranks, h->trunc_tol);
             h->t_trunc = t.stop();
         }
         // dense leaves (A4)
@@ -501,12 +543,16 @@ hm_status hm_factor(hm_handle h)
 {
     return guard(h, [&] {
         if (h->state != 2) throw HmError{HM_ERR_STATE, "hm_factor requires a filled, unfactored matrix"};
+        const bool zero_pivot = h->fault == HM_FAULT_ZERO_PIVOT;
+        if (zero_pivot) h->fault = HM_FAULT_NONE;
         h->flops_factor = 0;
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
         if (h->prm.precision == HM_FP32_REFINED) {
             // the FP64 H-matrix stays unfactored: it is the refinement operator
             Timer t(h->stream);
+            tile_free(h, h->tfac32);
+            h->tfac32 = nullptr;
             free_tree(h, h->blocks32);
             h->dirty32.clear();
             h->root32 = clone_tree<cf>(h, h->root, h->blocks32);
@@ -519,18 +565,35 @@ hm_status hm_factor(hm_handle h)
                     ranks.push_back(b->k);
                 }
             batched_truncate<cf>(h, lr, ranks, h->factor_tol);
+            if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
+                Block32 *d = first_diagonal_leaf(h->root32);
+                HM_CUDA(cudaMemsetAsync(d->D, 0, sizeof(cf) * d->nr, h->stream));
+            }
             hlu_factor<cf>(h, h->root32, h->factor_tol);
+            tile_free(h, h->tfac32);
+            h->tfac32 = tile_build<cf>(h, h->root32, true);
+            if (!h->tmat64) h->tmat64 = tile_build<zc>(h, h->root, false);
             h->t_factor = t.stop();
             h->state = 3;
             return;
         }
         if (h->prm.keep_matrix) {
+            tile_free(h, h->tmatcopy);
+            h->tmatcopy = nullptr;
             free_tree(h, h->copy_blocks);
             h->copy_root = clone_tree<zc>(h, h->root, h->copy_blocks);
         }
         Timer t(h->stream);
         h->dirty64.clear();
-        hlu_factor<zc>(h, h->root, h->tol);
+        if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
+            Block *d = first_diagonal_leaf(h->root);
+            HM_CUDA(cudaMemsetAsync(d->D, 0, sizeof(zc) * d->nr, h->stream));
+        }
+        tile_free(h, h->tmat64);  // the tree now holds the factors
+        h->tmat64 = nullptr;
+        hlu_factor<zc>(h, h->root, h->trunc_tol);
+        tile_free(h, h->tfac64);
+        h->tfac64 = tile_build<zc>(h, h->root, true);
         h->t_factor = t.stop();
         h->state = 3;
     });
@@ -558,6 +621,32 @@ __global__ void k_axpy1(const zc *__restrict__ d, zc *__restrict__ x, size_t n)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = zadd(x[i], d[i]);
+}
+
+// Number of non-finite real or imaginary parts among n complex values, added to *cnt.
+__global__ void k_nonfinite(const zc *__restrict__ x, size_t n, int *cnt)
+{
+    int bad = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        bad += !(isfinite(x[i].x) && isfinite(x[i].y));
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_down_sync(0xffffffff, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(cnt, bad);
+}
+
+// Throws HM_ERR_NUMERIC when x (n complex values, device) holds a NaN or an infinity.
+static void check_finite(hm_handle_s *h, const zc *x, size_t n, const char *what)
+{
+    int *d_cnt = (int *)dalloc(h, sizeof(int));
+    HM_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int), h->stream));
+    unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, 1024);
+    k_nonfinite<<<std::max(g, 1u), 256, 0, h->stream>>>(x, n, d_cnt);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+    int cnt = 0;
+    HM_CUDA(cudaMemcpyAsync(&cnt, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    dfree(h, d_cnt);
+    if (cnt) throw HmError{HM_ERR_NUMERIC, std::string(what) + ": " + std::to_string(cnt) + " non-finite values"};
 }
 
 static std::vector<double> colnorm2(hm_handle_s *h, const zc *X, int nrhs, double *d_tmp)
@@ -589,16 +678,25 @@ static bool refine_solve(hm_handle_s *h, int nrhs, const zc *b, zc *x)
     double worst = 1.0;
     for (it = 1; it <= h->prm.refine_max_iter; ++it) {
         convert_vec(h, r, r32, n);
-        hsolve<cf>(h, h->root32, MVT<cf>{r32, h->N, nrhs, h->N});
+        tile_solve<cf>(h, h->tfac32, r32, nrhs);
         convert_vec(h, r32, d, n);
         k_axpy1<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(d, x, n);
         HM_CHECK_LAUNCH();
         count_launch(h);
         HM_CUDA(cudaMemcpyAsync(r, b, sizeof(zc) * n, cudaMemcpyDeviceToDevice, h->stream));
-        hmatvec<zc>(h, h->root, MV{x, h->N, nrhs, h->N}, MV{r, h->N, nrhs, h->N}, zmake(-1, 0), false);
+        tile_matvec<zc>(h, h->tmat64, x, r, nrhs, zmake(-1, 0));
         std::vector<double> rn = colnorm2(h, r, nrhs, d_nrm);
         worst = 0;
-        for (int c = 0; c < nrhs; ++c) worst = std::max(worst, bn[c] > 0 ? std::sqrt(rn[c] / bn[c]) : 0.0);
+        bool finite = true;
+        for (int c = 0; c < nrhs; ++c) {
+            double q = bn[c] > 0 ? std::sqrt(rn[c] / bn[c]) : 0.0;
+            finite = finite && std::isfinite(q) && std::isfinite(bn[c]);
+            worst = std::max(worst, q);
+        }
+        if (!finite) {  // a NaN or an infinity: further steps cannot recover; the scan reports it
+            worst = std::numeric_limits<double>::infinity();
+            break;
+        }
         if (worst <= h->prm.refine_tol) {
             ok = true;
             break;
@@ -628,6 +726,12 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
     HM_CUDA(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, h->stream));
     zc *b = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * nrhs);
     launch_rhs(h, nrhs, d_dirs, b);
+    if (h->fault == HM_FAULT_NAN_RHS) {  // host-side injection: one right-hand-side entry is NaN
+        h->fault = HM_FAULT_NONE;
+        const zc nan = zmake(std::numeric_limits<double>::quiet_NaN(), 0.0);
+        HM_CUDA(cudaMemcpyAsync(b, &nan, sizeof(zc), cudaMemcpyHostToDevice, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+    }
     bool converged = true;
     if (h->prm.precision == HM_FP32_REFINED) {
         zc *x = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * nrhs);
@@ -635,7 +739,7 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
         launch_permute(h, nrhs, x, x_dev, h->d_iperm);
         dfree(h, x);
     } else {
-        hsolve<zc>(h, h->root, MV{b, h->N, nrhs, h->N});
+        tile_solve<zc>(h, h->tfac64, b, nrhs);
         launch_permute(h, nrhs, b, x_dev, h->d_iperm);
         h->refine_iters = 0;
         h->refine_res = 0;
@@ -643,6 +747,7 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
     dfree(h, b);
     dfree(h, d_dirs);
     h->t_solve = t.stop();  // also keeps the host vector alive until the copy is done
+    check_finite(h, x_dev, (size_t)h->N * nrhs, "hm_solve output");
     if (!converged)
         throw HmError{HM_ERR_NOT_CONVERGED, "iterative refinement did not reach refine_tol (residual " +
                                                 std::to_string(h->refine_res) + ")"};
@@ -687,19 +792,24 @@ hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const 
 hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev)
 {
     return guard(h, [&] {
+        TileOp<zc> **plan = nullptr;
         Block *A = nullptr;
-        if (h->state == 2 || (h->state == 3 && h->prm.precision == HM_FP32_REFINED))
+        if (h->state == 2 || (h->state == 3 && h->prm.precision == HM_FP32_REFINED)) {
             A = h->root;
-        else if (h->state == 3 && h->copy_root)
+            plan = &h->tmat64;
+        } else if (h->state == 3 && h->copy_root) {
             A = h->copy_root;
-        else
+            plan = &h->tmatcopy;
+        } else {
             throw HmError{HM_ERR_STATE, "hm_matvec needs a filled matrix (or keep_matrix before hm_factor)"};
+        }
         if (nrhs <= 0 || !x_dev || !y_dev) throw HmError{HM_ERR_ARG, "bad matvec arguments"};
+        if (!*plan) *plan = tile_build<zc>(h, A, false);
         size_t n = (size_t)h->N * nrhs;
         zc *xt = (zc *)dalloc(h, sizeof(zc) * n), *yt = (zc *)dalloc(h, sizeof(zc) * n);
         launch_permute(h, nrhs, (const zc *)x_dev, xt, h->d_perm);
         HM_CUDA(cudaMemsetAsync(yt, 0, sizeof(zc) * n, h->stream));
-        hmatvec(h, A, MV{xt, h->N, nrhs, h->N}, MV{yt, h->N, nrhs, h->N}, zmake(1, 0), false);
+        tile_matvec<zc>(h, *plan, xt, yt, nrhs, zmake(1, 0));
         launch_permute(h, nrhs, yt, (zc *)y_dev, h->d_iperm);
         dfree(h, xt);
         dfree(h, yt);
@@ -770,6 +880,14 @@ hm_status hm_query(hm_handle h, int what, double *out)
 }
 
 const char *hm_last_error(hm_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+hm_status hm_inject_fault(hm_handle h, int what)
+{
+    return guard(h, [&] {
+        if (what < HM_FAULT_NONE || what > HM_FAULT_ALLOC) throw HmError{HM_ERR_ARG, "unknown fault"};
+        h->fault = what;
+    });
+}
 
 hm_status hm_rank_samples(hm_handle h, int *n, float *feat_host, float *target_host)
 {

@@ -76,6 +76,9 @@ struct MVT {
 };
 typedef MVT<zc> MV;
 
+template <class C>
+struct TileOp;
+
 struct hm_handle_s {
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -138,7 +141,12 @@ struct hm_handle_s {
     int aca_nonconv = 0;
     unsigned long long near_points = 0;
     double tol = 1e-7;
+    double trunc_tol = 1e-7;     // truncation tolerance of the FP64 recompressions and H-LU
     double cur_tol = 1e-7;       // truncation tolerance of the factorisation in progress
+    int fault = 0;               // host-side fault injection armed by hm_inject_fault (HM_FAULT_*)
+    // block-row plans (hm_tiles.cu): product with the FP64 H-matrix, sweeps of the factors
+    TileOp<zc> *tmat64 = nullptr, *tmatcopy = nullptr, *tfac64 = nullptr;
+    TileOp<cf> *tfac32 = nullptr;
 };
 
 // ---- hm_mlp.cu ----
@@ -220,6 +228,21 @@ void free_tree(hm_handle_s *h, std::vector<BlockT<C> *> &owned);
 // y[i] = (To) x[i] for n complex values
 template <class Ti, class To>
 void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n);
+
+// ---- hm_tiles.cu (block-row product and substitution sweeps, complex128 and complex64) ----
+template <class C>
+struct TileOp;
+// Plan over the leaves of a block tree; factored: also the sweeps of its H-LU factors
+// (explicit inverses of the diagonal factors are formed here).  The plan points at the
+// leaves' data: it is valid while the tree's storage is unchanged.
+template <class C>
+TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored);
+template <class C>
+void tile_free(hm_handle_s *h, TileOp<C> *T);
+template <class C>
+void tile_matvec(hm_handle_s *h, TileOp<C> *T, const C *X, C *Y, int nrhs, C alpha);  // Y += alpha A X
+template <class C>
+void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs);  // X <- A^-1 X (factored plan)
 
 // ---- hm_planner.cpp ----
 void plan_geometry(hm_handle_s *h);  // nodes, near pairs, cluster tree, block tree

@@ -1,6 +1,8 @@
 // Excitation and outputs: plane-wave right-hand sides of the MFIE rows (Eq. 22:
 // b1 = -a_v . H_inc, b2 = a_u . H_inc; the paper's mu_1 row scale is dropped),
 // unknown permutations between natural and tree order, far field and RCS.
+#include <algorithm>
+
 #include "hm_internal.h"
 
 #define ETA0 376.730313668  // sqrt(mu0 / eps0), CODATA 2018
@@ -108,8 +110,15 @@ __global__ void k_farfield(const double *__restrict__ nodes, int nnode, double k
 void launch_farfield(hm_handle_s *h, int nrhs, const zc *d_x, int nang, const double *d_dirs, zc *d_efar, double *d_rcs)
 {
     if (nrhs <= 0 || nang <= 0) return;
-    k_farfield<<<dim3(nang, nrhs), 256, 0, h->stream>>>(h->d_nodes, h->nnode, h->prm.k0, d_x, nang, d_dirs, d_efar,
-                                                        d_rcs);
-    HM_CHECK_LAUNCH();
-    count_launch(h);
+    if (nang > 0x7fffffff / 4) throw HmError{HM_ERR_ARG, "too many observation directions"};
+    // gridDim.y is limited to 65,535: right-hand sides go in chunks of at most that many
+    for (int r0 = 0; r0 < nrhs; r0 += 65535) {
+        const int nr = std::min(65535, nrhs - r0);
+        k_farfield<<<dim3(nang, nr), 256, 0, h->stream>>>(h->d_nodes, h->nnode, h->prm.k0,
+                                                          d_x + (size_t)r0 * 2 * h->nnode, nang, d_dirs,
+                                                          d_efar ? d_efar + (size_t)r0 * nang * 3 : nullptr,
+                                                          d_rcs ? d_rcs + (size_t)r0 * nang : nullptr);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+    }
 }

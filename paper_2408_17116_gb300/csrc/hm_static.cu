@@ -21,7 +21,7 @@ const int kMaxDevices = 64;
 std::mutex g_mutex;
 double *g_scratch[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device.  In host code the
+// Device address of the scratch array on device dev, which must be current.  In host code the
 // array's name is a host-side stand-in, not a device address, so the address is
 // looked up once per device (with that device current) and cached.
 double *scratch_address(int dev)
@@ -54,9 +54,13 @@ extern "C" hm_status hm_farfield_static(hm_handle h, int nrhs, const void *x_dev
             throw HmError{HM_ERR_ARG, "3 nang + nrhs nang = " + std::to_string(need) +
                                           " doubles exceeds the static scratch of " +
                                           std::to_string(HM_FARFIELD_STATIC_DOUBLES)};
+        // the handle's stream belongs to the device the handle was created on; the array's
+        // address is looked up with that device current, before anything is copied
         int dev = 0;
         HM_CUDA(cudaGetDevice(&dev));
-        double *scr = scratch_address(dev);
+        if (dev != h->device)
+            throw HmError{HM_ERR_STATE, "hm_farfield_static: the current device is not the handle's device"};
+        double *scr = scratch_address(h->device);
         double *d_obs = scr, *d_rcs = rcs_host ? scr + 3 * (size_t)nang : nullptr;
         HM_CUDA(cudaMemcpyAsync(d_obs, obs_dirs, sizeof(double) * 3 * nang, cudaMemcpyHostToDevice, h->stream));
         launch_farfield(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);

@@ -1,0 +1,501 @@
+// Block-row form of the H-matrix product and of the H-forward/back substitution
+// (Sec. III.A, Eqs. 24-28) on the leaf partition of the block cluster tree.
+//
+// The diagonal blocks of the tree are dense leaves (c, c) of the leaf clusters c; they
+// partition the unknowns into row tiles.  Every other leaf (t, s) lies entirely left or
+// right of the diagonal and covers whole tiles of its row cluster t.  Restricted to the
+// rows of tile i, a dense leaf gives D[rows_i, :] and a low-rank leaf U[rows_i, :] V^H.
+//
+//   product:    y_i += sum over all leaves in block row i of (leaf rows_i) x_cols
+//   forward:    y_i  = L_ii^-1 P_i (b_i - sum_{leaves left of the diagonal} (leaf rows_i) y_cols)
+//   backward:   x_i  = U_ii^-1 (y_i - sum_{leaves right of the diagonal} (leaf rows_i) x_cols)
+//
+// This is the same arithmetic as the recursive substitution of the H-LU factors: the
+// recursion subtracts, level by level, L21 X1 from X2 before the permutation of a
+// diagonal leaf is applied to its own rows, so every tile receives exactly the sum of its
+// block row's left leaves times the final values of their columns.  Here each step of a
+// sweep is two launches: one CTA per chunk of the tile's pieces writes a partial sum, and
+// one CTA subtracts the partials in a fixed order, applies the pivots and multiplies by
+// the explicit inverse of the diagonal factor (computed once after the factorisation).
+// The product is one launch over every chunk of every tile plus one reduction launch.
+// Summation order is fixed, so results are deterministic.
+#include <algorithm>
+#include <cstring>
+
+#include "hm_internal.h"
+
+#define TL_T 256   // threads per CTA
+#define TL_NRB 4   // right-hand sides per pass
+#define TL_KC 128  // rank columns per pass of a low-rank piece
+#define TL_JC 256  // columns of a dense piece staged per pass
+
+template <class C>
+struct TPiece {
+    const C *A;     // dense: rows [rofs, rofs + rows) of D; low-rank: the same rows of U (ld = leaf rows)
+    const C *V;     // low-rank: V (ncol x k, ld = ncol); dense: null
+    int ld;         // leading dimension of A
+    int c0, ncol;   // columns of the leaf (tree order)
+    int k;          // rank (low-rank), 0 for dense
+};
+
+struct TChunk {
+    int p0, p1;   // pieces [p0, p1), all of one tile
+    int rows;     // rows of the tile
+    int slot;     // partial-sum slot
+};
+
+// acc[r][c] (shared, rows x nrb) += A[r, :] Z[:, c] for A (rows x n, ld) and Z staged in
+// shared memory (zs[j * TL_NRB + c], j < n).  Threads split the columns into G groups
+// that add their partial sums in group order (deterministic).
+template <class C, bool CONJ_Z>
+__device__ __forceinline__ void tile_gemv(const C *__restrict__ A, int ld, int rows, int n, const C *zs, int nrb,
+                                          C *acc)
+{
+    const int tid = threadIdx.x;
+    const int G = max(1, TL_T / rows);
+    const int r = tid % rows, g = tid / rows;
+    C a[TL_NRB];
+#pragma unroll
+    for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
+    if (g < G && tid < G * rows) {
+        for (int j = g; j < n; j += G) {
+            C v = A[(size_t)j * ld + r];
+#pragma unroll
+            for (int c = 0; c < TL_NRB; ++c)
+                if (c < nrb) a[c] = zfma(v, zs[j * TL_NRB + c], a[c]);
+        }
+    }
+    for (int gg = 0; gg < G; ++gg) {
+        if (g == gg && tid < G * rows) {
+#pragma unroll
+            for (int c = 0; c < TL_NRB; ++c)
+                if (c < nrb) acc[r * TL_NRB + c] = zadd(acc[r * TL_NRB + c], a[c]);
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per chunk: part[slot][c][i] = sum over the chunk's pieces of (piece rows) X(:, c).
+// X: tree-ordered columns, ld = ldx.  part: [slots][nrhs][rmax].
+template <class C>
+__global__ void __launch_bounds__(TL_T) k_tile_partial(const TPiece<C> *__restrict__ pieces,
+                                                         const TChunk *__restrict__ chunks, const C *__restrict__ X,
+                                                         int ldx, int nrhs, C *__restrict__ part, int rmax)
+{
+    __shared__ C acc[TL_T * TL_NRB];
+    __shared__ C zs[(TL_JC > TL_KC ? TL_JC : TL_KC) * TL_NRB];
+    const TChunk ch = chunks[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rows = ch.rows;
+    for (int cb = 0; cb < nrhs; cb += TL_NRB) {
+        const int nrb = min(TL_NRB, nrhs - cb);
+        for (int e = tid; e < rows * TL_NRB; e += TL_T) acc[e] = cmk<C>(0, 0);
+        __syncthreads();
+        for (int p = ch.p0; p < ch.p1; ++p) {
+            const TPiece<C> P = pieces[p];
+            if (P.k == 0) {
+                for (int j0 = 0; j0 < P.ncol; j0 += TL_JC) {
+                    const int n = min(TL_JC, P.ncol - j0);
+                    for (int e = tid; e < n * TL_NRB; e += TL_T) {
+                        int j = e / TL_NRB, c = e - j * TL_NRB;
+                        zs[e] = c < nrb ? X[(size_t)(cb + c) * ldx + P.c0 + j0 + j] : cmk<C>(0, 0);
+                    }
+                    __syncthreads();
+                    tile_gemv<C, false>(P.A + (size_t)j0 * P.ld, P.ld, rows, n, zs, nrb, acc);
+                }
+            } else {
+                for (int k0 = 0; k0 < P.k; k0 += TL_KC) {
+                    const int kc = min(TL_KC, P.k - k0);
+                    // t[kk][c] = sum_j conj(V[j, k0 + kk]) X[c0 + j, cb + c]: one warp per column kk
+                    for (int kk = warp; kk < kc; kk += TL_T / 32) {
+                        const C *v = P.V + (size_t)(k0 + kk) * P.ncol;
+                        C s[TL_NRB];
+#pragma unroll
+                        for (int c = 0; c < TL_NRB; ++c) s[c] = cmk<C>(0, 0);
+                        for (int j = lane; j < P.ncol; j += 32) {
+                            C vv = v[j];
+#pragma unroll
+                            for (int c = 0; c < TL_NRB; ++c)
+                                if (c < nrb) s[c] = zfmac(vv, X[(size_t)(cb + c) * ldx + P.c0 + j], s[c]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < TL_NRB; ++c) {
+                            for (int o = 16; o > 0; o >>= 1) {
+                                s[c].x += __shfl_down_sync(0xffffffff, s[c].x, o);
+                                s[c].y += __shfl_down_sync(0xffffffff, s[c].y, o);
+                            }
+                        }
+                        if (lane == 0) {
+#pragma unroll
+                            for (int c = 0; c < TL_NRB; ++c) zs[kk * TL_NRB + c] = c < nrb ? s[c] : cmk<C>(0, 0);
+                        }
+                    }
+                    __syncthreads();
+                    tile_gemv<C, false>(P.A + (size_t)k0 * P.ld, P.ld, rows, kc, zs, nrb, acc);
+                }
+            }
+        }
+        C *out = part + (size_t)ch.slot * nrhs * rmax;
+        for (int e = tid; e < rows * nrb; e += TL_T) {
+            int r = e / nrb, c = e - r * nrb;
+            out[(size_t)(cb + c) * rmax + r] = acc[r * TL_NRB + c];
+        }
+        __syncthreads();
+    }
+}
+
+// Product finish: one CTA per tile, Y[r0 + i, c] += alpha sum_{s in [s0, s1)} part[s][c][i].
+template <class C>
+__global__ void k_tile_reduce(const int *__restrict__ tr0, const int *__restrict__ trows,
+                              const int *__restrict__ ts0, const int *__restrict__ ts1, const C *__restrict__ part,
+                              int nrhs, int rmax, C alpha, C *Y, int ldy)
+{
+    const int t = blockIdx.x, r0 = tr0[t], rows = trows[t], s0 = ts0[t], s1 = ts1[t];
+    for (int e = threadIdx.x; e < rows * nrhs; e += blockDim.x) {
+        int c = e / rows, i = e - c * rows;
+        C s = cmk<C>(0, 0);
+        for (int q = s0; q < s1; ++q) s = zadd(s, part[((size_t)q * nrhs + c) * rmax + i]);
+        C &y = Y[(size_t)c * ldy + r0 + i];
+        y = zfma(alpha, s, y);
+    }
+}
+
+// Sweep step finish (one CTA): z = X[r0 .. r0 + rows, :] - sum_{s < nslots} part[s] (fixed
+// order); forward: z = P z (the diagonal leaf's pivots, applied in order); then
+// X[r0 .., :] = Minv z with Minv the explicit inverse of the tile's triangular factor.
+template <class C>
+__global__ void __launch_bounds__(TL_T) k_tile_finish(int r0, int rows, int nslots, const C *__restrict__ part,
+                                                        int nrhs, int rmax, const int *__restrict__ piv,
+                                                        const C *__restrict__ Minv, C *X, int ldx)
+{
+    extern __shared__ __align__(16) unsigned char tf_raw[];
+    C *z = (C *)tf_raw;  // [rows][TL_NRB]
+    const int tid = threadIdx.x;
+    for (int cb = 0; cb < nrhs; cb += TL_NRB) {
+        const int nrb = min(TL_NRB, nrhs - cb);
+        for (int e = tid; e < rows * TL_NRB; e += TL_T) {
+            int i = e / TL_NRB, c = e - i * TL_NRB;
+            C s = cmk<C>(0, 0);
+            if (c < nrb) {
+                s = X[(size_t)(cb + c) * ldx + r0 + i];
+                for (int q = 0; q < nslots; ++q) s = zsub(s, part[((size_t)q * nrhs + cb + c) * rmax + i]);
+            }
+            z[e] = s;
+        }
+        __syncthreads();
+        if (piv && tid < nrb) {
+            for (int k = 0; k < rows; ++k) {
+                int p = piv[k];
+                if (p != k) {
+                    C tmp = z[k * TL_NRB + tid];
+                    z[k * TL_NRB + tid] = z[p * TL_NRB + tid];
+                    z[p * TL_NRB + tid] = tmp;
+                }
+            }
+        }
+        __syncthreads();
+        C a[TL_NRB];
+        for (int e = tid; e < rows; e += TL_T) {
+#pragma unroll
+            for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
+            for (int j = 0; j < rows; ++j) {
+                C m = Minv[(size_t)j * rows + e];
+#pragma unroll
+                for (int c = 0; c < TL_NRB; ++c) a[c] = zfma(m, z[j * TL_NRB + c], a[c]);
+            }
+            for (int c = 0; c < nrb; ++c) X[(size_t)(cb + c) * ldx + r0 + e] = a[c];
+        }
+        __syncthreads();
+    }
+}
+
+template <class C>
+__global__ void k_tile_identity(C *I, int n)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < (size_t)n * n) I[idx] = cmk<C>((idx % n) == (idx / n) ? 1 : 0, 0);
+}
+
+template <class C>
+static void identity_fill(hm_handle_s *h, C *I, int n)
+{
+    size_t nn = (size_t)n * n;
+    k_tile_identity<C><<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(I, n);
+    HM_CHECK_LAUNCH();
+    count_launch(h);
+}
+
+template <class C>
+struct TileOp {
+    int N = 0, ntile = 0, rmax = 0;
+    std::vector<int> r0, rows;              // tiles
+    // product over all leaves
+    TPiece<C> *d_pa = nullptr;
+    TChunk *d_ca = nullptr;
+    int nca = 0;
+    int *d_tr0 = nullptr, *d_trows = nullptr, *d_ts0 = nullptr, *d_ts1 = nullptr;
+    // sweeps of a factored tree
+    bool factored = false;
+    TPiece<C> *d_pl = nullptr, *d_pu = nullptr;
+    TChunk *d_cl = nullptr, *d_cu = nullptr;
+    std::vector<int> cl0, cl1, cu0, cu1;  // chunk ranges per tile
+    int maxchunks = 0;
+    C *d_inv = nullptr;                   // per tile: L^-1 then U^-1 (rows x rows each)
+    std::vector<size_t> inv_off;
+    std::vector<const int *> piv;         // per tile: the diagonal leaf's pivots (device)
+    std::vector<void *> owned;
+};
+
+namespace {
+
+template <class C>
+void collect(BlockT<C> *b, std::vector<BlockT<C> *> &out)
+{
+    if (b->type == B_HIER) {
+        for (int i = 0; i < 4; ++i) collect(b->ch[i], out);
+    } else {
+        out.push_back(b);
+    }
+}
+
+template <class C>
+double piece_cost(const TPiece<C> &p, int rows)
+{
+    return p.k ? (double)p.k * (rows + p.ncol) : (double)rows * p.ncol;
+}
+
+// Chunks of one tile's pieces, each of at most `target` cost (at least one piece).
+template <class C>
+void make_chunks(const std::vector<TPiece<C>> &pcs, int p0, int p1, int rows, double target,
+                 std::vector<TChunk> &out, int &slot)
+{
+    int s = p0;
+    double acc = 0;
+    for (int p = p0; p < p1; ++p) {
+        double c = piece_cost(pcs[p], rows);
+        if (p > s && acc + c > target) {
+            out.push_back(TChunk{s, p, rows, slot++});
+            s = p;
+            acc = 0;
+        }
+        acc += c;
+    }
+    if (p1 > s) out.push_back(TChunk{s, p1, rows, slot++});
+}
+
+template <class T>
+T *upload(hm_handle_s *h, const std::vector<T> &v, std::vector<void *> &owned)
+{
+    T *d = (T *)dalloc(h, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (!v.empty()) HM_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->stream));
+    owned.push_back(d);
+    return d;
+}
+
+}  // namespace
+
+template <class C>
+TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
+{
+    TileOp<C> *T = new TileOp<C>();
+    try {
+        std::vector<BlockT<C> *> leaves;
+        collect(root, leaves);
+        std::vector<BlockT<C> *> diag;
+        for (BlockT<C> *b : leaves)
+            if (b->r0 == b->c0 && b->nr == b->nc && b->type == B_DENSE) diag.push_back(b);
+        std::sort(diag.begin(), diag.end(), [](BlockT<C> *a, BlockT<C> *b) { return a->r0 < b->r0; });
+        int pos = 0;
+        for (BlockT<C> *d : diag) {
+            if (d->r0 != pos) throw HmError{HM_ERR_STATE, "tile plan: diagonal leaves do not partition the unknowns"};
+            if (d->nr > TL_T) throw HmError{HM_ERR_ARG, "tile plan: a leaf cluster has more than 256 unknowns"};
+            T->r0.push_back(d->r0);
+            T->rows.push_back(d->nr);
+            T->rmax = std::max(T->rmax, d->nr);
+            pos += d->nr;
+        }
+        T->N = pos;
+        T->ntile = (int)diag.size();
+        auto tile_of = [&](int r) {
+            int i = (int)(std::upper_bound(T->r0.begin(), T->r0.end(), r) - T->r0.begin()) - 1;
+            return i;
+        };
+        // pieces per tile: all / left of the diagonal / right of the diagonal
+        std::vector<std::vector<TPiece<C>>> all(T->ntile), left(T->ntile), right(T->ntile);
+        for (BlockT<C> *b : leaves) {
+            if (b->type == B_LR && b->k == 0) continue;
+            const bool isdiag = b->r0 == b->c0 && b->type == B_DENSE && b->nr == b->nc;
+            for (int i = tile_of(b->r0); i < T->ntile && T->r0[i] < b->r0 + b->nr; ++i) {
+                if (T->r0[i] < b->r0 || T->r0[i] + T->rows[i] > b->r0 + b->nr)
+                    throw HmError{HM_ERR_STATE, "tile plan: a leaf does not cover whole tiles"};
+                const int rofs = T->r0[i] - b->r0;
+                TPiece<C> p;
+                p.ld = b->nr;
+                p.c0 = b->c0;
+                p.ncol = b->nc;
+                if (b->type == B_DENSE) {
+                    p.A = b->D + rofs;
+                    p.V = nullptr;
+                    p.k = 0;
+                } else {
+                    p.A = b->U + rofs;
+                    p.V = b->V;
+                    p.k = b->k;
+                }
+                all[i].push_back(p);
+                if (isdiag) continue;
+                if (b->c0 + b->nc <= T->r0[i])
+                    left[i].push_back(p);
+                else if (b->c0 >= T->r0[i] + T->rows[i])
+                    right[i].push_back(p);
+                else
+                    throw HmError{HM_ERR_STATE, "tile plan: an off-diagonal leaf crosses the diagonal"};
+            }
+        }
+        // product plan: chunks sized so that the launch has a few CTAs per SM
+        {
+            std::vector<TPiece<C>> pcs;
+            std::vector<TChunk> chs;
+            std::vector<int> s0(T->ntile), s1(T->ntile);
+            double tot = 0;
+            for (int i = 0; i < T->ntile; ++i)
+                for (auto &p : all[i]) tot += piece_cost(p, T->rows[i]);
+            const double target = std::max(tot / (4.0 * 152.0), 1.0);
+            int slot = 0;
+            for (int i = 0; i < T->ntile; ++i) {
+                int p0 = (int)pcs.size();
+                pcs.insert(pcs.end(), all[i].begin(), all[i].end());
+                s0[i] = slot;
+                make_chunks(pcs, p0, (int)pcs.size(), T->rows[i], target, chs, slot);
+                s1[i] = slot;
+            }
+            T->nca = (int)chs.size();
+            T->d_pa = upload(h, pcs, T->owned);
+            T->d_ca = upload(h, chs, T->owned);
+            T->d_tr0 = upload(h, T->r0, T->owned);
+            T->d_trows = upload(h, T->rows, T->owned);
+            T->d_ts0 = upload(h, s0, T->owned);
+            T->d_ts1 = upload(h, s1, T->owned);
+        }
+        if (factored) {
+            T->factored = true;
+            std::vector<TPiece<C>> pl, pu;
+            std::vector<TChunk> cl, cu;
+            T->cl0.resize(T->ntile);
+            T->cl1.resize(T->ntile);
+            T->cu0.resize(T->ntile);
+            T->cu1.resize(T->ntile);
+            for (int i = 0; i < T->ntile; ++i) {
+                // about 2 CTAs per SM per step
+                double tl = 0, tu = 0;
+                for (auto &p : left[i]) tl += piece_cost(p, T->rows[i]);
+                for (auto &p : right[i]) tu += piece_cost(p, T->rows[i]);
+                int sl = 0, su = 0;
+                int p0 = (int)pl.size();
+                pl.insert(pl.end(), left[i].begin(), left[i].end());
+                T->cl0[i] = (int)cl.size();
+                make_chunks(pl, p0, (int)pl.size(), T->rows[i], std::max(tl / 304.0, 1.0), cl, sl);
+                T->cl1[i] = (int)cl.size();
+                p0 = (int)pu.size();
+                pu.insert(pu.end(), right[i].begin(), right[i].end());
+                T->cu0[i] = (int)cu.size();
+                make_chunks(pu, p0, (int)pu.size(), T->rows[i], std::max(tu / 304.0, 1.0), cu, su);
+                T->cu1[i] = (int)cu.size();
+                T->maxchunks = std::max(T->maxchunks, std::max(sl, su));
+            }
+            T->d_pl = upload(h, pl, T->owned);
+            T->d_pu = upload(h, pu, T->owned);
+            T->d_cl = upload(h, cl, T->owned);
+            T->d_cu = upload(h, cu, T->owned);
+            // explicit inverses of the diagonal factors: L^-1 (unit lower) and U^-1
+            size_t tot = 0;
+            for (int i = 0; i < T->ntile; ++i) {
+                T->inv_off.push_back(tot);
+                tot += 2 * (size_t)T->rows[i] * T->rows[i];
+            }
+            T->d_inv = (C *)dalloc(h, sizeof(C) * std::max<size_t>(tot, 1));
+            T->owned.push_back(T->d_inv);
+            for (int i = 0; i < T->ntile; ++i) {
+                const int n = T->rows[i];
+                C *Li = T->d_inv + T->inv_off[i], *Ui = Li + (size_t)n * n;
+                identity_fill(h, Li, n);
+                identity_fill(h, Ui, n);
+                ztrsm_lln(h, diag[i]->D, n, n, MVT<C>{Li, n, n, n});
+                ztrsm_lun(h, diag[i]->D, n, n, MVT<C>{Ui, n, n, n});
+                T->piv.push_back(diag[i]->piv);
+            }
+        }
+    } catch (...) {
+        tile_free(h, T);
+        throw;
+    }
+    return T;
+}
+
+template <class C>
+void tile_free(hm_handle_s *h, TileOp<C> *T)
+{
+    if (!T) return;
+    for (void *p : T->owned) dfree(h, p);
+    delete T;
+}
+
+// Y += alpha A X (tree order; X, Y: N x nrhs with ld N).
+template <class C>
+void tile_matvec(hm_handle_s *h, TileOp<C> *T, const C *X, C *Y, int nrhs, C alpha)
+{
+    if (nrhs <= 0 || T->ntile == 0) return;
+    C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->nca, 1) * nrhs * T->rmax);
+    if (T->nca) {
+        k_tile_partial<C><<<T->nca, TL_T, 0, h->stream>>>(T->d_pa, T->d_ca, X, T->N, nrhs, part, T->rmax);
+        HM_CHECK_LAUNCH();
+    }
+    k_tile_reduce<C><<<T->ntile, TL_T, 0, h->stream>>>(T->d_tr0, T->d_trows, T->d_ts0, T->d_ts1, part, nrhs,
+                                                        T->rmax, alpha, Y, T->N);
+    HM_CHECK_LAUNCH();
+    count_launch(h, T->nca ? 2 : 1);
+    dfree(h, part);
+}
+
+// X <- A^-1 X with the H-LU factors (tree order, N x nrhs, ld N).
+template <class C>
+void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
+{
+    if (!T->factored) throw HmError{HM_ERR_STATE, "tile_solve on an unfactored plan"};
+    if (nrhs <= 0 || T->ntile == 0) return;
+    C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->maxchunks, 1) * nrhs * T->rmax);
+    const size_t smem = sizeof(C) * (size_t)T->rmax * TL_NRB;
+    for (int i = 0; i < T->ntile; ++i) {
+        const int nch = T->cl1[i] - T->cl0[i];
+        if (nch) {
+            k_tile_partial<C><<<nch, TL_T, 0, h->stream>>>(T->d_pl, T->d_cl + T->cl0[i], X, T->N, nrhs, part, T->rmax);
+            HM_CHECK_LAUNCH();
+        }
+        const C *Li = T->d_inv + T->inv_off[i];
+        k_tile_finish<C><<<1, TL_T, smem, h->stream>>>(T->r0[i], T->rows[i], nch, part, nrhs, T->rmax, T->piv[i], Li,
+                                                       X, T->N);
+        HM_CHECK_LAUNCH();
+        count_launch(h, nch ? 2 : 1);
+    }
+    for (int i = T->ntile - 1; i >= 0; --i) {
+        const int nch = T->cu1[i] - T->cu0[i];
+        if (nch) {
+            k_tile_partial<C><<<nch, TL_T, 0, h->stream>>>(T->d_pu, T->d_cu + T->cu0[i], X, T->N, nrhs, part, T->rmax);
+            HM_CHECK_LAUNCH();
+        }
+        const C *Ui = T->d_inv + T->inv_off[i] + (size_t)T->rows[i] * T->rows[i];
+        k_tile_finish<C><<<1, TL_T, smem, h->stream>>>(T->r0[i], T->rows[i], nch, part, nrhs, T->rmax, nullptr, Ui,
+                                                       X, T->N);
+        HM_CHECK_LAUNCH();
+        count_launch(h, nch ? 2 : 1);
+    }
+    dfree(h, part);
+}
+
+#define HM_INST_TILES(Z)                                                              \
+    template TileOp<Z> *tile_build<Z>(hm_handle_s *, BlockT<Z> *, bool);              \
+    template void tile_free<Z>(hm_handle_s *, TileOp<Z> *);                           \
+    template void tile_matvec<Z>(hm_handle_s *, TileOp<Z> *, const Z *, Z *, int, Z); \
+    template void tile_solve<Z>(hm_handle_s *, TileOp<Z> *, Z *, int);
+HM_INST_TILES(zc)
+HM_INST_TILES(cf)

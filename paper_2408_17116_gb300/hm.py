@@ -24,6 +24,8 @@ Q = dict(N=0, NNODE=1, NPATCH=2, NEAR_PAIRS=3, DENSE_BLOCKS=4, LR_BLOCKS=5, CR=6
          KCORE_FLOPS=38, KCORE_LAUNCHES=39)
 RANK_NFEAT = 8
 HM_FP64, HM_FP32_REFINED = 0, 1
+HM_PEC_MFIE, HM_PEC_CFIE, HM_DIEL_MULLER = 0, 1, 2
+FAULT = dict(NONE=0, ZERO_PIVOT=1, NAN_RHS=2, ALLOC=3)
 
 EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor", "hm_solve",
            "hm_solve_host", "hm_farfield", "hm_matvec", "hm_query", "hm_last_error", "hm_destroy",
@@ -32,14 +34,16 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
            "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host",
-           "hm_muller_rhs_farfield_host")
+           "hm_muller_rhs_farfield_host", "hm_inject_fault")
 
 
 class hm_params(ctypes.Structure):
     _fields_ = [("k0", ctypes.c_double), ("formulation", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("eta", ctypes.c_double), ("aca_tol", ctypes.c_double), ("near_delta", ctypes.c_double),
                 ("aca_max_rank", ctypes.c_int), ("precision", ctypes.c_int), ("keep_matrix", ctypes.c_int),
-                ("factor_tol", ctypes.c_double), ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int)]
+                ("factor_tol", ctypes.c_double), ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int),
+                ("cfie_alpha", ctypes.c_double), ("eps_r_re", ctypes.c_double), ("eps_r_im", ctypes.c_double),
+                ("mu_r", ctypes.c_double), ("trunc_tol", ctypes.c_double), ("quad_order", ctypes.c_int)]
 
 
 class hm_body(ctypes.Structure):
@@ -82,6 +86,7 @@ def load(path=SO):
     L.hm_muller_near_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, I, I, I, D, P]
     L.hm_muller_rhs_farfield_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, P, P, P, P, I, P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
+    L.hm_inject_fault.argtypes = [P, I]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
     L.hm_get_nodes_host.argtypes = [P, P]
@@ -228,12 +233,17 @@ class Solver:
             pass
 
     def hm_build_geometry(self, bodies, ms, nc, k0, leaf, eta, aca_tol, near_delta=0.5, aca_max_rank=0,
-                          keep_matrix=False, precision=HM_FP64, factor_tol=0.0, refine_tol=0.0, refine_max_iter=0):
+                          keep_matrix=False, precision=HM_FP64, factor_tol=0.0, refine_tol=0.0, refine_max_iter=0,
+                          formulation=HM_PEC_MFIE, cfie_alpha=0.0, eps_r=1.0, mu_r=0.0, trunc_tol=0.0,
+                          quad_order=0):
         self._bodies = make_bodies(bodies, ms)
-        p = hm_params(k0=float(k0), formulation=0, leaf=int(leaf), eta=float(eta), aca_tol=float(aca_tol),
-                      near_delta=float(near_delta), aca_max_rank=int(aca_max_rank), precision=int(precision),
-                      keep_matrix=int(bool(keep_matrix)), factor_tol=float(factor_tol),
-                      refine_tol=float(refine_tol), refine_max_iter=int(refine_max_iter))
+        eps = complex(eps_r)
+        p = hm_params(k0=float(k0), formulation=int(formulation), leaf=int(leaf), eta=float(eta),
+                      aca_tol=float(aca_tol), near_delta=float(near_delta), aca_max_rank=int(aca_max_rank),
+                      precision=int(precision), keep_matrix=int(bool(keep_matrix)), factor_tol=float(factor_tol),
+                      refine_tol=float(refine_tol), refine_max_iter=int(refine_max_iter),
+                      cfie_alpha=float(cfie_alpha), eps_r_re=eps.real, eps_r_im=eps.imag, mu_r=float(mu_r),
+                      trunc_tol=float(trunc_tol), quad_order=int(quad_order))
         self._check(self.L.hm_build_geometry(self.h, self._bodies, len(ms), int(nc), ctypes.byref(p)))
         self.N = int(self.hm_query("N"))
         self.nnode = self.N // 2
@@ -288,6 +298,9 @@ class Solver:
         y = self.torch.empty_like(x)
         self._check(self.L.hm_matvec(self.h, x.shape[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
         return y
+
+    def hm_inject_fault(self, what):
+        self._check(self.L.hm_inject_fault(self.h, FAULT[what] if isinstance(what, str) else int(what)))
 
     def hm_query(self, key):
         out = ctypes.c_double()

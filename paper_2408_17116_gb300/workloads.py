@@ -5,9 +5,11 @@ none of the method's arithmetic lives here.  Every body is a cube-mapped
 ellipsoid (6 m^2 curvilinear patches, the patch family of the paper's sphere
 experiments, Sec. IV: 24..4056 patches = 6 m^2), wavelength 1 m (k = 2 pi).
 
-Random incidence angles use numpy's Philox counter-based generator
-(Philox4x64-10) seeded with 2408017116: theta = arccos(1 - 2U), phi = 2 pi U,
-polarisation = theta-hat.
+Random incidence angles use numpy's Philox counter-based generator, the
+Philox4x64-10 variant (not Philox4x32-10), seeded with 2408017116:
+theta = arccos(1 - 2U), phi = 2 pi U, polarisation = theta-hat.  Every consumer
+(library tests, oracle, benchmark) draws them from this module, so both sides of a
+parity check see the same angles.
 """
 import numpy as np
 
@@ -65,7 +67,7 @@ def workload(name):
         kh, pol = incidence(2, SEED + 1)
         return dict(name=name, bodies=body(semi=(1.0,) * 3)[None], ms=[2], nc=6, k=K0,
                     leaf=40, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol, radius=1.0)
-    if name == "ellipsoid_small":  # rotated, off-centre ellipsoid, 1,536 unknowns
+    if name == "ellipsoid_small":  # rotated, off-centre ellipsoid, 3,072 unknowns
         th = 0.3
         R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
         kh, pol = incidence(3, SEED + 2)

@@ -56,6 +56,18 @@ def test_binding_constants_match_the_header():
     assert {v: k for k, v in st.items()} == hm.STATUS
     prec = _header_enum("HM_FP")
     assert prec == {"HM_FP64": hm.HM_FP64, "HM_FP32_REFINED": hm.HM_FP32_REFINED}
+    form = dict(_header_enum("HM_PEC_"), **_header_enum("HM_DIEL_"))
+    assert form == {"HM_PEC_MFIE": hm.HM_PEC_MFIE, "HM_PEC_CFIE": hm.HM_PEC_CFIE,
+                    "HM_DIEL_MULLER": hm.HM_DIEL_MULLER}
+
+
+def test_params_struct_carries_the_boundary_fields():
+    # the solver parameters named by the paper's problem statement (formulation, CFIE weight,
+    # interior material, tolerances, quadrature order) are all part of the ABI struct
+    names = [f for f, _ in hm.hm_params._fields_]
+    for f in ("k0", "formulation", "cfie_alpha", "eps_r_re", "eps_r_im", "mu_r", "leaf", "eta", "aca_tol",
+              "trunc_tol", "near_delta", "quad_order", "precision"):
+        assert f in names, f
 
 
 def test_binding_struct_layouts_match_the_header(tmp_path):

@@ -101,7 +101,13 @@ def test_entries_rows(name):
         assert np.max(np.abs(got - ref)) <= 2e-8 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("name", SMALL)
+# Low-rank leaves each workload must produce after ACA (a floor, not the count): the
+# 1-wavelength sphere at leaf 64 has admissible blocks whose ACA all reach the rank bound
+# of a 64 x 64 block (32), so every one of them ends up dense; the others compress.
+MIN_LOWRANK = {"sphere_d1_m1_nc8": 0, "sphere_d2_m2_nc6": 1, "ellipsoid_small": 1, "sphere_d4_m2_nc10": 100}
+
+
+@pytest.mark.parametrize("name", SMALL + ["sphere_d4_m2_nc10"])
 def test_leaf_blocks_against_dense(name):
     wl, o, A, b, x = oracle_for(name)
     s = make_solver(wl)
@@ -109,9 +115,12 @@ def test_leaf_blocks_against_dense(name):
     perm = s.perm()
     Ap = A[np.ix_(perm, perm)]
     blocks = s.blocks()
-    assert blocks[:, 2].sum() > 0
+    lowrank = blocks[:, 0] == 1
+    assert lowrank.sum() >= MIN_LOWRANK[name], (name, int(lowrank.sum()), len(blocks))
+    assert (blocks[lowrank, 5] >= 1).all()
     # every (row, col) pair is covered exactly once by the leaves
     cover = np.zeros((o.N, o.N), dtype=np.int8)
+    nchecked = 0
     for i, (typ, r0, nr, c0, ncol, k) in enumerate(blocks):
         cover[r0:r0 + nr, c0:c0 + ncol] += 1
         ref = Ap[r0:r0 + nr, c0:c0 + ncol]
@@ -122,6 +131,8 @@ def test_leaf_blocks_against_dense(name):
         else:
             assert err <= 10 * wl["aca_tol"], (i, err, k)
             assert k <= nr * ncol / (nr + ncol)
+            nchecked += 1
+    assert nchecked == lowrank.sum()
     assert (cover == 1).all()
 
 
@@ -169,6 +180,24 @@ def test_matvec_against_dense_oracle():
     s.hm_factor()  # keep_matrix: the unfactored copy still serves hm_matvec
     y2 = s.hm_matvec(torch.tensor(xr, device="cuda")).cpu().numpy()
     assert np.linalg.norm(y2 - ref) / np.linalg.norm(ref) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_mid_size_solution_against_dense_oracle(precision):
+    # 4,800 unknowns (4-wavelength sphere, leaf 128): hundreds of low-rank leaves, so the
+    # H-LU's formatted products and recompressions are exercised, in both precisions
+    wl, o, A, b, xo = oracle_for("sphere_d4_m2_nc10")
+    prec = hm.HM_FP64 if precision == "fp64" else hm.HM_FP32_REFINED
+    s = make_solver(wl, precision=prec)
+    s.hm_fill()
+    assert s.hm_query("LR_BLOCKS") >= MIN_LOWRANK["sphere_d4_m2_nc10"]
+    s.hm_factor()
+    x = s.hm_solve(wl["kdirs"], wl["pols"]).cpu().numpy()
+    for r in range(x.shape[0]):
+        err = np.linalg.norm(x[r] - xo[r]) / np.linalg.norm(xo[r])
+        res = np.linalg.norm(A @ x[r] - b[r]) / np.linalg.norm(b[r])
+        assert err <= 1e-5, (precision, r, err)
+        assert res <= 1e-5, (precision, r, res)
 
 
 def test_no_admissible_blocks_reduces_to_block_dense_lu():
@@ -231,6 +260,33 @@ def test_fp32_refinement_reports_non_convergence():
         s.hm_solve(wl["kdirs"], wl["pols"])
     assert e.value.status == 6
     assert s.hm_query("REFINE_ITERS") == 1
+
+
+def test_full_size_fp32_refined_against_stored_dense_solution():
+    # 19,200 unknowns (8-wavelength sphere, the benchmark workload) against the dense
+    # oracle's solution, stored by tests/golden/make_dense_solution.py (oracle fill + dense LU)
+    import json
+    import os
+    name = "sphere_d8_m4_nc10"
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + "_x")
+    xo = np.load(gold + ".npy")
+    meta = json.load(open(gold + ".json"))
+    wl = workloads.workload(name)
+    s = make_solver(wl, precision=hm.HM_FP32_REFINED)
+    s.hm_fill()
+    s.hm_factor()
+    x = s.hm_solve(wl["kdirs"], wl["pols"]).cpu().numpy()
+    assert s.hm_query("REFINE_RES") <= 1e-10
+    assert x.shape == xo.shape
+    for r in range(x.shape[0]):
+        err = np.linalg.norm(x[r] - xo[r]) / np.linalg.norm(xo[r])
+        assert err <= 1e-5, (r, err)
+        # full residual, bounded through |A|_2 <= sqrt(|A|_1 |A|_inf) of the oracle's matrix:
+        # |A x - b| <= |A|_2 |x - x_o| + |A x_o - b|
+        bound = meta["norm2_bound"] * np.linalg.norm(x[r] - xo[r]) / meta["bnorm"][r] + meta["residual"][r]
+        assert bound <= 1e-5, (r, bound)
+        # element by element: every unknown within 1e-5 of the largest one of its solution
+        assert np.max(np.abs(x[r] - xo[r])) <= 1e-5 * np.max(np.abs(xo[r])), r
 
 
 def test_full_size_fp32_refined_sampled_residual():
