@@ -76,6 +76,7 @@ def lib():
         L.or_rhs_muller.argtypes = [P, i32, P, P, P]
         L.or_currents_muller.argtypes = [P, P, P, P]
         L.or_farfield_muller.argtypes = [P, P, i32, P, P, P]
+        L.or_set_cfie.argtypes = [P, f64]
         _lib = L
     return _lib
 
@@ -136,7 +137,7 @@ class Oracle:
     independent self/near integrator (box rule and Duffy rule).
     """
 
-    def __init__(self, bodies, ms, nc, k, delta=0.5, q=12, qd=20):
+    def __init__(self, bodies, ms, nc, k, delta=0.5, q=12, qd=20, cfie_alpha=None):
         self.bodies = np.ascontiguousarray(np.asarray(bodies, dtype=np.float64).reshape(-1, 15))
         self.ms = np.ascontiguousarray(np.asarray(ms, dtype=np.int32).reshape(-1))
         self.nc, self.k, self.delta = int(nc), float(k), float(delta)
@@ -147,6 +148,10 @@ class Oracle:
         self.nnode = lib().or_num_nodes(self._h)
         self.npatch = lib().or_num_patches(self._h)
         self.N = 2 * self.nnode
+        self.cfie_alpha = cfie_alpha
+        if cfie_alpha is not None:
+            # PEC combined field equation alpha EFIE / eta0 + (1 - alpha) MFIE (Eq. 10, both rows)
+            lib().or_set_cfie(self._h, float(cfie_alpha))
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -213,6 +213,11 @@ typedef struct {
      * its wavenumber k2 = k sqrt(eps_r); mu_r = 1 */
     int dielectric;
     cplx epsr, k2;
+    /* PEC combined field equation: weight alpha of the EFIE row, and the 1-D spectral
+     * differentiation matrix dmat[l * nc + l'] = ell_{l'}'(x_l) */
+    int cfie;
+    double alpha;
+    double *dmat;
 } or_ctx;
 
 static void ctx_patch_map(const or_ctx *c, int p, double u, double v, double *r, double *ru, double *rv)
@@ -336,7 +341,7 @@ void or_destroy(or_ctx *c)
 {
     if (!c) return;
     free(c->bodies); free(c->pbody); free(c->pface); free(c->pi); free(c->pj);
-    free(c->nodes1d); free(c->fejer);
+    free(c->nodes1d); free(c->fejer); free(c->dmat);
     free(c->nr); free(c->nau); free(c->nav); free(c->nn); free(c->nsg); free(c->nw);
     free(c->bbmin); free(c->bbmax); free(c->near);
     free(c->glx); free(c->glw); free(c->gdx); free(c->gdw);
@@ -379,7 +384,7 @@ void or_patch_point(const or_ctx *c, int p, double u, double v, double *r, doubl
 /* Kernels                                                                    */
 /* ------------------------------------------------------------------------- */
 
-enum { KIND_SINGLE = 0, KIND_MFIE = 1, KIND_MULLER = 2 };
+enum { KIND_SINGLE = 0, KIND_MFIE = 1, KIND_MULLER = 2, KIND_EVEC = 3, KIND_SCALAR = 4 };
 
 typedef struct {
     const or_ctx *c;
@@ -390,6 +395,7 @@ typedef struct {
     double k;
     double tgt[3], tu[3], tv[3];
     int ncomp;
+    double te[2][3];  /* KIND_EVEC: the target's test vectors sqrtG a^u, sqrtG a^v (Eqs. 17-18) */
     cplx *W;       /* ncomp x nc^2, index [comp][kv*nc + lu] */
     /* planar test map (used when p < 0): r = (a u, b v, 0) */
     double pa, pb;
@@ -509,7 +515,20 @@ static void integ_point(integ *ig, double u, double v, double wt)
     double d[3] = {ig->tgt[0] - r[0], ig->tgt[1] - r[1], ig->tgt[2] - r[2]};
     double R = norm3(d);
     cplx kv[4];
-    if (ig->kind == KIND_SINGLE) {
+    if (ig->kind == KIND_EVEC || ig->kind == KIND_SCALAR) {
+        /* G(R) t_b . a_a (vector potential part of the EFIE, tested), or G(R) alone (the
+         * scalar potential of the surface divergence); no Jacobian: J dS' = F^a a_a du dv
+         * and (div J) dS' = (d_u F^u + d_v F^v) du dv */
+        cplx G = cexp(-I * ig->k * R) / (4.0 * OR_PI * R);
+        if (ig->kind == KIND_SCALAR) {
+            kv[0] = G;
+        } else {
+            kv[0] = G * dot3(ig->te[0], ru);
+            kv[1] = G * dot3(ig->te[0], rv);
+            kv[2] = G * dot3(ig->te[1], ru);
+            kv[3] = G * dot3(ig->te[1], rv);
+        }
+    } else if (ig->kind == KIND_SINGLE) {
         double cr[3];
         cross3(ru, rv, cr);
         /* G(R) = exp(-jkR) / (4 pi R)  (Eq. 4), times the surface Jacobian */
@@ -725,6 +744,10 @@ void or_planar_single_layer(const or_ctx *c, double a, double b, double k, const
 /* Matrix rows, dense matrix                                                  */
 /* ------------------------------------------------------------------------- */
 
+static void node_rows_cfie(const or_ctx *c, int i, cplx *row_u, cplx *row_v, cplx *scratch);
+static void matrix_dense_cfie(const or_ctx *c, cplx *A);
+static void test_vectors(const or_ctx *c, int i, double t[2][3]);
+
 /* Both rows (u and v) of target node i of the MFIE system, length N = 2 nnode each.
  * Unknown index 2*node + a (a = 0: F^u, a = 1: F^v). */
 static void node_rows(const or_ctx *c, int i, cplx *row_u, cplx *row_v, cplx *W)
@@ -773,11 +796,14 @@ void or_matrix_rows(const or_ctx *c, int nrows, const int *rows, cplx *out)
     {
         cplx *ru = (cplx *)malloc(sizeof(cplx) * N);
         cplx *rv = (cplx *)malloc(sizeof(cplx) * N);
-        cplx *W = (cplx *)malloc(sizeof(cplx) * 4 * nc2);
+        cplx *W = (cplx *)malloc(sizeof(cplx) * 4 * nc2 * (c->cfie ? 2 : 1));
 #pragma omp for schedule(dynamic, 1)
         for (int t = 0; t < nrows; ++t) {
             int r = rows[t];
-            node_rows(c, r / 2, ru, rv, W);
+            if (c->cfie)
+                node_rows_cfie(c, r / 2, ru, rv, W);
+            else
+                node_rows(c, r / 2, ru, rv, W);
             memcpy(out + (size_t)t * N, (r % 2 == 0) ? ru : rv, sizeof(cplx) * N);
         }
         free(ru);
@@ -791,6 +817,10 @@ void or_matrix_dense(const or_ctx *c, cplx *A)
 {
     int N = 2 * c->nnode;
     int nc2 = c->nc * c->nc;
+    if (c->cfie) {
+        matrix_dense_cfie(c, A);
+        return;
+    }
 #pragma omp parallel
     {
         cplx *ru = (cplx *)malloc(sizeof(cplx) * N);
@@ -836,6 +866,236 @@ void or_single_layer_dense(const or_ctx *c, cplx *S)
             }
         }
         free(W);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* PEC combined field equation (Eq. 10, both rows; combination not in the paper) */
+/* ------------------------------------------------------------------------- */
+/*
+ * Row b of node i:  alpha E_b + (1 - alpha) M_b,  with M_b the MFIE row above and
+ *   E_b = t_b . (jk S[J] - (1/(jk)) grad S[div J])  (the EFIE operator L_E of Eq. 2
+ *         divided by eta0), t_b = sqrtG a^b (Eqs. 17-18): t_u = a_v x n, t_v = n x a_u;
+ *   right-hand side alpha t_b . E_inc / eta0 + (1 - alpha) t_b . (n x H_inc).
+ * The surface divergence of the interpolated current is its spectral derivative on the
+ * source patch: (div J) dS' = (d_u F^u + d_v F^v) du dv (Eq. 11).
+ * Far pairs (Nystrom / Fejer rule, grad G analytic):
+ *   E_b(i; j,a) = jk w_j G_ij t_b.a_a(j) - (1/(jk)) sum_{j' on the a-line of j} w_j' g_ij' t_b.(r_i - r_j') D[l(j'), l(j)]
+ * Self/near pairs: the vector part is the exact integral of G t_b.a_a against the
+ * cardinal function; grad S[div J] is strongly singular, so it is taken as the tangential
+ * derivative of the scalar potential Phi = S[div J] along the target patch:
+ *   t_b . grad Phi (r_i) = sqrtG_i (g^{bu} d_u Phi + g^{bv} d_v Phi)(i),
+ * with Phi at the target patch's nodes from the exact integrals of G against the
+ * source-differentiated cardinal functions, and d_u, d_v the spectral derivatives on
+ * the target patch (g^{bc}: inverse metric of a_u, a_v at the target).
+ */
+void or_set_cfie(or_ctx *c, double alpha)
+{
+    int nc = c->nc;
+    c->cfie = 1;
+    c->alpha = alpha;
+    if (!c->dmat) c->dmat = (double *)malloc(sizeof(double) * nc * nc);
+    double ell[64];
+    for (int l = 0; l < nc; ++l) cheb_cardinal_d(nc, c->nodes1d, c->nodes1d[l], ell, c->dmat + l * nc);
+}
+
+/* Test vectors t_u = a_v x n, t_v = n x a_u of node i. */
+static void test_vectors(const or_ctx *c, int i, double t[2][3])
+{
+    cross3(c->nav + 3 * i, c->nn + 3 * i, t[0]);
+    cross3(c->nn + 3 * i, c->nau + 3 * i, t[1]);
+}
+
+/* The integrals of one kind for target node tn over source patch p. */
+static void near_kind(const or_ctx *c, int kind, int tn, int p, cplx *W)
+{
+    integ ig;
+    memset(&ig, 0, sizeof(ig));
+    ig.c = c;
+    ig.kind = kind;
+    ig.p = p;
+    ig.k = c->k;
+    ig.kbox = c->k;
+    ig.ncomp = kind == KIND_SCALAR ? 1 : 4;
+    ig.W = W;
+    for (int d = 0; d < 3; ++d) ig.tgt[d] = c->nr[3 * tn + d];
+    test_vectors(c, tn, ig.te);
+    int nc = c->nc, tp = tn / (nc * nc);
+    if (tp == p)
+        integ_patch(&ig, tn % nc, (tn / nc) % nc);
+    else
+        integ_patch(&ig, -1, -1);
+}
+
+/* CFIE entries of the rows of target nodes `tl` (local indices on patch q) against source
+ * patch p, a near pair: out[(2 t + b) * 2 nc^2 + 2 j + a] for t < ntl (the identity term
+ * (1 - alpha)/2 is not included).  Phi is needed at every node of the two lines of
+ * each target through its patch; the integrals of each such node are computed once. */
+static void cfie_near_rows(const or_ctx *c, int q, int p, int ntl, const int *tl, cplx *out)
+{
+    int nc = c->nc, nc2 = nc * nc, w = 2 * nc2;
+    const double *D = c->dmat;
+    const cplx jk = I * c->k;
+    unsigned char *need = (unsigned char *)calloc(nc2, 1);
+    for (int t = 0; t < ntl; ++t) {
+        int li = tl[t] % nc, ki = tl[t] / nc;
+        for (int l = 0; l < nc; ++l) {
+            need[ki * nc + l] = 1;
+            need[l * nc + li] = 1;
+        }
+    }
+    /* Phi_a(i'; j) = sum_j' W^S(i'; j') Dsrc_a(j', j) for the needed targets i' */
+    cplx *WS = (cplx *)malloc(sizeof(cplx) * nc2);
+    cplx *Phi = (cplx *)calloc((size_t)nc2 * 2 * nc2, sizeof(cplx)); /* [i'][a][j] */
+    for (int ip = 0; ip < nc2; ++ip) {
+        if (!need[ip]) continue;
+        near_kind(c, KIND_SCALAR, q * nc2 + ip, p, WS);
+        cplx *Pu = Phi + (size_t)ip * 2 * nc2, *Pv = Pu + nc2;
+        for (int kv = 0; kv < nc; ++kv)
+            for (int lu = 0; lu < nc; ++lu) {
+                cplx su = 0, sv = 0;
+                for (int l2 = 0; l2 < nc; ++l2) su += WS[kv * nc + l2] * D[l2 * nc + lu];
+                for (int k2 = 0; k2 < nc; ++k2) sv += WS[k2 * nc + lu] * D[k2 * nc + kv];
+                Pu[kv * nc + lu] = su;
+                Pv[kv * nc + lu] = sv;
+            }
+    }
+    cplx *WV = (cplx *)malloc(sizeof(cplx) * 4 * nc2), *WM = (cplx *)malloc(sizeof(cplx) * 4 * nc2);
+    for (int t = 0; t < ntl; ++t) {
+        int il = tl[t], li = il % nc, ki = il / nc, tn = q * nc2 + il;
+        near_kind(c, KIND_EVEC, tn, p, WV);
+        or_near_block(c, tn, p, WM);
+        const double *au = c->nau + 3 * tn, *av = c->nav + 3 * tn;
+        double guu = dot3(au, au), guv = dot3(au, av), gvv = dot3(av, av);
+        double det = guu * gvv - guv * guv, sg = c->nsg[tn];
+        double gi[2][2] = {{gvv / det, -guv / det}, {-guv / det, guu / det}}; /* g^{bc} */
+        for (int a = 0; a < 2; ++a)
+            for (int j = 0; j < nc2; ++j) {
+                /* d_u Phi_a and d_v Phi_a at the target (spectral derivative on patch q) */
+                cplx du = 0, dv = 0;
+                for (int l2 = 0; l2 < nc; ++l2) du += D[li * nc + l2] * Phi[((size_t)(ki * nc + l2) * 2 + a) * nc2 + j];
+                for (int k2 = 0; k2 < nc; ++k2) dv += D[ki * nc + k2] * Phi[((size_t)(k2 * nc + li) * 2 + a) * nc2 + j];
+                for (int b = 0; b < 2; ++b) {
+                    cplx E = jk * WV[(2 * b + a) * nc2 + j] - (1.0 / jk) * sg * (gi[b][0] * du + gi[b][1] * dv);
+                    cplx M = WM[(2 * b + a) * nc2 + j];
+                    out[(size_t)(2 * t + b) * w + 2 * j + a] = c->alpha * E + (1.0 - c->alpha) * M;
+                }
+            }
+    }
+    free(need);
+    free(WS);
+    free(Phi);
+    free(WV);
+    free(WM);
+}
+
+/* CFIE far entries of node i's two rows against every node of source patch p
+ * (row_u, row_v: full-length rows, written at p's columns). */
+static void cfie_far_rows(const or_ctx *c, int i, int p, cplx *row_u, cplx *row_v, cplx *h)
+{
+    int nc = c->nc, nc2 = nc * nc;
+    const double *D = c->dmat;
+    const cplx jk = I * c->k;
+    const double *ri = c->nr + 3 * i, *aui = c->nau + 3 * i, *avi = c->nav + 3 * i;
+    double t[2][3];
+    test_vectors(c, i, t);
+    /* h[b][j'] = w_j' g(R) t_b . (r_i - r_j') */
+    for (int j = 0; j < nc2; ++j) {
+        int sn = p * nc2 + j;
+        const double *rj = c->nr + 3 * sn;
+        double d[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
+        double R = norm3(d);
+        cplx g = -(1.0 + I * c->k * R) * cexp(-I * c->k * R) / (4.0 * OR_PI * R * R * R) * c->nw[sn];
+        h[j] = g * dot3(t[0], d);
+        h[nc2 + j] = g * dot3(t[1], d);
+    }
+    for (int j = 0; j < nc2; ++j) {
+        int sn = p * nc2 + j, lu = j % nc, kv = j / nc;
+        const double *rj = c->nr + 3 * sn, *auj = c->nau + 3 * sn, *avj = c->nav + 3 * sn;
+        double d[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
+        double R = norm3(d);
+        cplx ex = cexp(-I * c->k * R);
+        cplx G = ex / (4.0 * OR_PI * R) * c->nw[sn];
+        cplx g = -(1.0 + I * c->k * R) * ex / (4.0 * OR_PI * R * R * R) * c->nw[sn];
+        double cu[3], cv[3];
+        cross3(d, auj, cu);
+        cross3(d, avj, cv);
+        cplx M[2][2] = {{g * dot3(avi, cu), g * dot3(avi, cv)}, {-g * dot3(aui, cu), -g * dot3(aui, cv)}};
+        for (int b = 0; b < 2; ++b) {
+            cplx divu = 0, divv = 0;
+            for (int l2 = 0; l2 < nc; ++l2) divu += h[b * nc2 + kv * nc + l2] * D[l2 * nc + lu];
+            for (int k2 = 0; k2 < nc; ++k2) divv += h[b * nc2 + k2 * nc + lu] * D[k2 * nc + kv];
+            cplx Eu = jk * G * dot3(t[b], auj) - (1.0 / jk) * divu;
+            cplx Ev = jk * G * dot3(t[b], avj) - (1.0 / jk) * divv;
+            cplx *row = b == 0 ? row_u : row_v;
+            row[2 * sn] = c->alpha * Eu + (1.0 - c->alpha) * M[b][0];
+            row[2 * sn + 1] = c->alpha * Ev + (1.0 - c->alpha) * M[b][1];
+        }
+    }
+}
+
+/* Both CFIE rows of node i (full length N). */
+static void node_rows_cfie(const or_ctx *c, int i, cplx *row_u, cplx *row_v, cplx *scratch)
+{
+    int nc = c->nc, nc2 = nc * nc, w = 2 * nc2;
+    int ti = i / nc2, il = i - ti * nc2;
+    for (int p = 0; p < c->npatch; ++p) {
+        if (c->near[(size_t)ti * c->npatch + p]) {
+            cfie_near_rows(c, ti, p, 1, &il, scratch);
+            for (int col = 0; col < w; ++col) {
+                row_u[p * w + col] = scratch[col];
+                row_v[p * w + col] = scratch[w + col];
+            }
+        } else {
+            cfie_far_rows(c, i, p, row_u, row_v, scratch);
+        }
+    }
+    row_u[2 * i] += 0.5 * (1.0 - c->alpha);
+    row_v[2 * i + 1] += 0.5 * (1.0 - c->alpha);
+}
+
+/* Dense CFIE matrix, column-major, assembled by target patch so that the scalar
+ * potentials of each near pair are integrated once per target node. */
+static void matrix_dense_cfie(const or_ctx *c, cplx *A)
+{
+    int N = 2 * c->nnode, nc = c->nc, nc2 = nc * nc, w = 2 * nc2;
+#pragma omp parallel
+    {
+        cplx *blk = (cplx *)malloc(sizeof(cplx) * (size_t)w * w);
+        cplx *ru = (cplx *)malloc(sizeof(cplx) * N), *rv = (cplx *)malloc(sizeof(cplx) * N);
+        cplx *h = (cplx *)malloc(sizeof(cplx) * 2 * nc2);
+        int *all = (int *)malloc(sizeof(int) * nc2);
+        for (int t = 0; t < nc2; ++t) all[t] = t;
+#pragma omp for schedule(dynamic, 1)
+        for (int q = 0; q < c->npatch; ++q) {
+            for (int p = 0; p < c->npatch; ++p) {
+                if (c->near[(size_t)q * c->npatch + p]) {
+                    cfie_near_rows(c, q, p, nc2, all, blk);
+                    for (int r = 0; r < w; ++r)
+                        for (int col = 0; col < w; ++col)
+                            A[(size_t)(p * w + col) * N + q * w + r] = blk[(size_t)r * w + col];
+                } else {
+                    for (int il = 0; il < nc2; ++il) {
+                        int i = q * nc2 + il;
+                        cfie_far_rows(c, i, p, ru, rv, h);
+                        for (int col = p * w; col < (p + 1) * w; ++col) {
+                            A[(size_t)col * N + 2 * i] = ru[col];
+                            A[(size_t)col * N + 2 * i + 1] = rv[col];
+                        }
+                    }
+                }
+            }
+            for (int il = 0; il < nc2; ++il) {
+                int i = q * nc2 + il;
+                A[(size_t)(2 * i) * N + 2 * i] += 0.5 * (1.0 - c->alpha);
+                A[(size_t)(2 * i + 1) * N + 2 * i + 1] += 0.5 * (1.0 - c->alpha);
+            }
+        }
+        free(blk);
+        free(ru);
+        free(rv);
+        free(h);
+        free(all);
     }
 }
 
@@ -1018,8 +1278,18 @@ void or_rhs(const or_ctx *c, int nrhs, const double *kdir, const double *pol, cp
             cplx ph = cexp(-I * c->k * dot3(kh, c->nr + 3 * i)) / c->eta0;
             cplx hv[3] = {h0[0] * ph, h0[1] * ph, h0[2] * ph};
             const double *au = c->nau + 3 * i, *av = c->nav + 3 * i;
-            b[(size_t)r * N + 2 * i] = -(av[0] * hv[0] + av[1] * hv[1] + av[2] * hv[2]);
-            b[(size_t)r * N + 2 * i + 1] = au[0] * hv[0] + au[1] * hv[1] + au[2] * hv[2];
+            cplx bu = -(av[0] * hv[0] + av[1] * hv[1] + av[2] * hv[2]);
+            cplx bv = au[0] * hv[0] + au[1] * hv[1] + au[2] * hv[2];
+            if (c->cfie) {
+                /* alpha t_b . E_inc / eta0 + (1 - alpha) t_b . (n x H_inc) */
+                double t[2][3];
+                test_vectors(c, i, t);
+                const double *pl = pol + 3 * r;
+                bu = c->alpha * dot3(t[0], pl) * ph + (1.0 - c->alpha) * bu;
+                bv = c->alpha * dot3(t[1], pl) * ph + (1.0 - c->alpha) * bv;
+            }
+            b[(size_t)r * N + 2 * i] = bu;
+            b[(size_t)r * N + 2 * i + 1] = bv;
         }
     }
 }
