@@ -223,6 +223,12 @@ hm_status hm_matvec(hm_handle h, int nrhs, const void *x_dev, void *y_dev);
 hm_status hm_query(hm_handle h, int what, double *out);
 const char *hm_last_error(hm_handle h);
 
+/* Recompression batches since the last hm_fill or hm_factor began: *nbatches receives the
+ * count; out (may be NULL) receives [nbatches][7] = jobs, largest m or n, largest K, sum of
+ * (m + n) K^2, device seconds of the QR launch, device seconds of the core launch, host wall
+ * seconds of the batch.  Diagnostics for the recompression kernels; synchronises. */
+hm_status hm_get_trunc_log_host(hm_handle h, int *nbatches, double *out);
+
 /* Host-side fault injection for tests of the error paths (the paper has no counterpart).
  * Arms one fault for the next call that reaches it; no GPU fault, trap or hang is caused.
  *   HM_FAULT_ZERO_PIVOT: hm_factor zeroes the first column of the first diagonal leaf before

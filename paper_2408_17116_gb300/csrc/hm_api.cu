@@ -315,6 +315,7 @@ hm_status hm_fill(hm_handle h)
         const int nc = h->nc, w = 2 * nc * nc;
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
+        h->trunc_log.clear();
         // near-field quadrature (A3)
         {
             Timer t(h->stream);
@@ -548,6 +549,7 @@ hm_status hm_factor(hm_handle h)
         h->flops_factor = 0;
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
+        h->trunc_log.clear();
         if (h->prm.precision == HM_FP32_REFINED) {
             // the FP64 H-matrix stays unfactored: it is the refinement operator
             Timer t(h->stream);
@@ -880,6 +882,15 @@ hm_status hm_query(hm_handle h, int what, double *out)
 }
 
 const char *hm_last_error(hm_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+hm_status hm_get_trunc_log_host(hm_handle h, int *nbatches, double *out)
+{
+    return guard(h, [&] {
+        if (!nbatches) throw HmError{HM_ERR_ARG, "null count"};
+        *nbatches = (int)(h->trunc_log.size() / 7);
+        if (out) std::copy(h->trunc_log.begin(), h->trunc_log.end(), out);
+    });
+}
 
 hm_status hm_inject_fault(hm_handle h, int what)
 {

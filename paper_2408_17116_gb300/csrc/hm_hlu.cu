@@ -489,8 +489,18 @@ void hlu_factor(hm_handle_s *h, BlockT<Z> *root, double tol)
     h->cur_tol = tol;
     int *d_info = (int *)dalloc(h, sizeof(int));
     HM_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), h->stream));
-    hlu_rec(h, root, d_info);
-    flush(h, root);
+    h->d_info_cur = d_info;
+    try {
+        hlu_rec(h, root, d_info);
+        flush(h, root);
+    } catch (...) {
+        h->d_info_cur = nullptr;
+        h->cur_tol = saved;
+        cudaStreamSynchronize(h->stream);
+        dfree(h, d_info);
+        throw;
+    }
+    h->d_info_cur = nullptr;
     int info = 0;
     HM_CUDA(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     HM_CUDA(cudaStreamSynchronize(h->stream));

@@ -136,6 +136,10 @@ struct hm_handle_s {
     // recompression kernels: Householder QR of the factors, and the core factorisation
     // (pivoted QR for complex64, Jacobi SVD for complex128); reset with the statistics
     double kqr_s = 0, kqr_flops = 0, kqr_n = 0, kcore_s = 0, kcore_flops = 0, kcore_n = 0;
+    // one record per recompression batch (reset with the statistics): jobs, largest m or n,
+    // largest K, sum of (m + n) K^2, device seconds of the QR and of the core kernel, host
+    // wall seconds of the whole batch
+    std::vector<double> trunc_log;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     long long launches = 0;
     int aca_nonconv = 0;
@@ -144,6 +148,7 @@ struct hm_handle_s {
     double trunc_tol = 1e-7;     // truncation tolerance of the FP64 recompressions and H-LU
     double cur_tol = 1e-7;       // truncation tolerance of the factorisation in progress
     int fault = 0;               // host-side fault injection armed by hm_inject_fault (HM_FAULT_*)
+    int *d_info_cur = nullptr;   // zero-pivot flag of the H-LU in progress (device), else null
     // block-row plans (hm_tiles.cu): product with the FP64 H-matrix, sweeps of the factors
     TileOp<zc> *tmat64 = nullptr, *tmatcopy = nullptr, *tfac64 = nullptr;
     TileOp<cf> *tfac32 = nullptr;
@@ -199,6 +204,16 @@ template <class C>
 void zcopy2d(hm_handle_s *h, MVT<C> dst, MVT<C> src);
 template <class C>
 void zscale_cols(hm_handle_s *h, MVT<C> X, const typename CReal<C>::R *d_s);  // X[:,j] *= s[j]
+// Householder QR of many matrices in one cooperative launch (hm_qr.cu): A (m x K, ld m)
+// is overwritten; Q (m x r, ld m) and R (r x K, ld r) with r = min(m, K) are written.
+template <class C>
+struct QRJob {
+    C *A;
+    int m, K;
+    C *Q, *R;
+};
+template <class C>
+void batched_qr(hm_handle_s *h, const std::vector<QRJob<C>> &jobs);
 // Truncated recompression of A = U V^H (U m x K, V n x K): returns the new rank;
 // *Uo, *Vo receive freshly allocated factors (balanced: both scaled by sqrt(sigma)).
 template <class C>

@@ -264,6 +264,9 @@ __global__ void __launch_bounds__(1024) k_getrf(int n, C *A, int lda, int *piv, 
                     v = sv[w];
                     ii = si[w];
                 }
+            // a column without a finite entry leaves no valid argmax: no interchange (the
+            // zero / non-finite pivot is reported through info below)
+            if (ii < k || ii >= n) ii = k;
             s_p = ii;
             piv[k] = ii;
             if (!(v > 0)) {
@@ -697,12 +700,12 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc<C> *__restrict__ de
     }
     __syncthreads();
     // order by decreasing S (ties: lower index first): each column's rank is the number
-    // of columns that precede it
+    // of columns that precede it; a NaN norm sorts last so that ord stays a permutation
     for (int j = tid; j < q; j += SVD_T) {
-        const R sj = d.S[j];
+        const R sj = d.S[j] == d.S[j] ? d.S[j] : (R)-1;
         int rank = 0;
         for (int i = 0; i < q; ++i) {
-            const R si = d.S[i];
+            const R si = d.S[i] == d.S[i] ? d.S[i] : (R)-1;
             rank += (si > sj) || (si == sj && i < j);
         }
         d.ord[rank] = j;
@@ -712,13 +715,18 @@ __global__ void __launch_bounds__(SVD_T) k_svd(const SVDDesc<C> *__restrict__ de
 // Assemble the truncated factors: Uo[:, t] = Q_U * (X col ord[t]) / S * sqrt(S) ... done as
 // gather + scale: G[:, t] = M[:, ord[t]] * f(S), H[:, t] = Y[:, ord[t]] * sqrt(S)
 template <class C>
-__global__ void k_gather_cols(const C *M, int p, const int *ord, const typename CReal<C>::R *S, int kk, C *G, int mode)
+__global__ void k_gather_cols(const C *M, int p, const int *ord, const typename CReal<C>::R *S, int kk, int q, C *G,
+                              int mode)
 {
     typedef typename CReal<C>::R R;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)p * kk) return;
     int i = (int)(idx % p), t = (int)(idx / p);
     int c = ord[t];
+    if (c < 0 || c >= q) {  // never taken after the host's check of ord; keeps the access in bounds
+        G[(size_t)t * p + i] = cmk<C>(0, 0);
+        return;
+    }
     R s = S[c];
     R f;
     if (mode == 0)
@@ -943,7 +951,7 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
     typedef typename CReal<C>::R R;
     const bool qrcp = std::is_same<C, cf>::value;
     // workspace and copies
-    std::vector<QRDesc<C>> qd;
+    std::vector<QRJob<C>> qd;
     for (auto &J : jobs) {
         J.r1 = std::min(J.m, J.K);
         J.r2 = std::min(J.n, J.K);
@@ -961,19 +969,15 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
         J.ord = (int *)dalloc(h, sizeof(int) * (J.r2 + 1));
         zcopy2d(h, MVT<C>{J.Ua, J.m, J.K, J.m}, MVT<C>{(C *)J.U, J.m, J.K, J.ldu});
         zcopy2d(h, MVT<C>{J.Va, J.n, J.K, J.n}, MVT<C>{(C *)J.V, J.n, J.K, J.ldv});
-        qd.push_back(QRDesc<C>{J.Ua, J.m, J.K, J.QU, J.RU, J.bU});
-        qd.push_back(QRDesc<C>{J.Va, J.n, J.K, J.QV, J.RV, J.bV});
+        qd.push_back(QRJob<C>{J.Ua, J.m, J.K, J.QU, J.RU});
+        qd.push_back(QRJob<C>{J.Va, J.n, J.K, J.QV, J.RV});
         h->flops_factor += 16.0 * ((double)J.m + J.n) * J.K * J.K;
     }
-    QRDesc<C> *d_qd = (QRDesc<C> *)dalloc(h, sizeof(QRDesc<C>) * qd.size());
-    HM_CUDA(cudaMemcpyAsync(d_qd, qd.data(), sizeof(QRDesc<C>) * qd.size(), cudaMemcpyHostToDevice, h->stream));
     for (int e = 0; e < 4; ++e)
         if (!h->ev[e]) HM_CUDA(cudaEventCreate(&h->ev[e]));
     HM_CUDA(cudaEventRecord(h->ev[0], h->stream));
-    k_qr<C><<<(unsigned)qd.size(), QR_T, 0, h->stream>>>(d_qd);
-    HM_CHECK_LAUNCH();
+    batched_qr<C>(h, qd);
     HM_CUDA(cudaEventRecord(h->ev[1], h->stream));
-    count_launch(h);
     for (auto &J : jobs) h->kqr_flops += householder_flops(J.m, J.K, J.r1) + householder_flops(J.n, J.K, J.r2);
     // core M = R_U R_V^H
     for (auto &J : jobs)
@@ -1005,7 +1009,6 @@ static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
     HM_CHECK_LAUNCH();
     HM_CUDA(cudaEventRecord(h->ev[3], h->stream));
     count_launch(h);
-    dfree(h, d_qd);
     dfree(h, d_desc);  // stream-ordered: released after the kernel
 }
 
@@ -1050,6 +1053,9 @@ template <class C>
 static int trunc_stage2(hm_handle_s *h, TruncJob<C> &J, const std::vector<double> &S, const std::vector<int> &ord,
                         double tol, C **Uo, C **Vo)
 {
+    for (size_t t = 0; t < S.size(); ++t)
+        if (!std::isfinite(S[t]) || ord[t] < 0 || ord[t] >= (int)S.size())
+            throw HmError{HM_ERR_NUMERIC, "recompression of a block with non-finite values"};
     double tot = 0;
     for (double s : S) tot += s * s;
     int kk = (int)S.size();
@@ -1069,8 +1075,8 @@ static int trunc_stage2(hm_handle_s *h, TruncJob<C> &J, const std::vector<double
         G = (C *)dalloc(h, sizeof(C) * (size_t)J.r1 * kk);
         Hh = (C *)dalloc(h, sizeof(C) * (size_t)J.r2 * kk);
         size_t n1 = (size_t)J.r1 * kk, n2 = (size_t)J.r2 * kk;
-        k_gather_cols<C><<<(unsigned)((n1 + 255) / 256), 256, 0, h->stream>>>(J.Mc, J.r1, J.ord, J.S, kk, G, 0);
-        k_gather_cols<C><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(J.Y, J.r2, J.ord, J.S, kk, Hh, 1);
+        k_gather_cols<C><<<(unsigned)((n1 + 255) / 256), 256, 0, h->stream>>>(J.Mc, J.r1, J.ord, J.S, kk, J.r2, G, 0);
+        k_gather_cols<C><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(J.Y, J.r2, J.ord, J.S, kk, J.r2, Hh, 1);
         HM_CHECK_LAUNCH();
         count_launch(h, 2);
         *Uo = (C *)dalloc(h, sizeof(C) * (size_t)J.m * kk);
@@ -1093,6 +1099,17 @@ static int trunc_stage2(hm_handle_s *h, TruncJob<C> &J, const std::vector<double
     return kk;
 }
 
+// During an H-LU the zero-pivot flag of the diagonal leaves is read at every
+// synchronisation of a recompression batch, so a singular leaf stops the factorisation
+// before its non-finite values reach a rank decision.
+static void check_pivots(hm_handle_s *h)
+{
+    if (!h->d_info_cur) return;
+    int info = 0;
+    HM_CUDA(cudaMemcpy(&info, h->d_info_cur, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info) throw HmError{HM_ERR_SINGULAR, "H-LU: zero pivot in a diagonal leaf"};
+}
+
 template <class C>
 static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector<std::vector<double>> &S,
                      std::vector<std::vector<int>> &ord)
@@ -1106,7 +1123,12 @@ static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector
         for (size_t i = 0; i < jobs.size(); ++i)
             HM_CUDA(cudaMemcpyAsync(&rk[i], jobs[i].ord + jobs[i].r2, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         HM_CUDA(cudaStreamSynchronize(h->stream));
-        for (size_t i = 0; i < jobs.size(); ++i) ord[i].assign(1, rk[i]);
+        check_pivots(h);
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            if (rk[i] < 0 || rk[i] > std::min(jobs[i].r1, jobs[i].r2))
+                throw HmError{HM_ERR_NUMERIC, "recompression rank out of range"};
+            ord[i].assign(1, rk[i]);
+        }
         return;
     }
     std::vector<std::vector<R>> Sr(jobs.size());
@@ -1117,6 +1139,7 @@ static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector
         HM_CUDA(cudaMemcpyAsync(ord[i].data(), jobs[i].ord, sizeof(int) * jobs[i].r2, cudaMemcpyDeviceToHost, h->stream));
     }
     HM_CUDA(cudaStreamSynchronize(h->stream));
+    check_pivots(h);
     for (size_t i = 0; i < jobs.size(); ++i) S[i].assign(Sr[i].begin(), Sr[i].end());
 }
 
@@ -1176,12 +1199,18 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
             idx.push_back(i);
         }
         if (jobs.empty()) continue;
+        auto tb = std::chrono::steady_clock::now();
         h->tr_batches += 1;
         h->tr_jobs += (double)jobs.size();
+        double bmm = 0, bmk = 0, bw = 0;
         for (auto &J : jobs) {
             h->tr_maxk = std::max(h->tr_maxk, (double)J.K);
             h->tr_work += ((double)J.m + J.n) * J.K * J.K;
+            bmm = std::max(bmm, (double)std::max(J.m, J.n));
+            bmk = std::max(bmk, (double)J.K);
+            bw += ((double)J.m + J.n) * J.K * J.K;
         }
+        const double q0 = h->kqr_s, c0 = h->kcore_s;
         double saved = h->cur_tol;
         h->cur_tol = tol;
         trunc_stage1(h, jobs);
@@ -1203,6 +1232,9 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
             b->V = Vo;
             b->k = kk;
         }
+        const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
+        const double rec[7] = {(double)jobs.size(), bmm, bmk, bw, h->kqr_s - q0, h->kcore_s - c0, wall};
+        h->trunc_log.insert(h->trunc_log.end(), rec, rec + 7);
     }
     h->tr_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -34,7 +34,7 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
            "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host",
-           "hm_muller_rhs_farfield_host", "hm_inject_fault")
+           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host")
 
 
 class hm_params(ctypes.Structure):
@@ -87,6 +87,7 @@ def load(path=SO):
     L.hm_muller_rhs_farfield_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, P, P, P, P, I, P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_inject_fault.argtypes = [P, I]
+    L.hm_get_trunc_log_host.argtypes = [P, ctypes.POINTER(I), P]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
     L.hm_get_nodes_host.argtypes = [P, P]
@@ -298,6 +299,14 @@ class Solver:
         y = self.torch.empty_like(x)
         self._check(self.L.hm_matvec(self.h, x.shape[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
         return y
+
+    def trunc_log(self):
+        """Per recompression batch: jobs, max m|n, max K, sum (m+n) K^2, QR s, core s, wall s."""
+        n = ctypes.c_int()
+        self._check(self.L.hm_get_trunc_log_host(self.h, ctypes.byref(n), None))
+        out = np.empty((n.value, 7))
+        self._check(self.L.hm_get_trunc_log_host(self.h, ctypes.byref(n), _np_ptr(out)))
+        return out
 
     def hm_inject_fault(self, what):
         self._check(self.L.hm_inject_fault(self.h, FAULT[what] if isinstance(what, str) else int(what)))
