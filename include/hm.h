@@ -89,6 +89,11 @@ typedef struct {
                              H-LU (0 = aca_tol) */
     int quad_order;       /* Gauss points per direction of the self/near rule's inner panels and Duffy squares
                              (0 = 24; 4..36; the outer panels take ceil(2 quad_order / 3)) */
+    int factor_leaf;      /* the H-LU stores, as one dense block each, the hierarchical blocks of the
+                             first cluster level whose clusters hold at most factor_leaf unknowns (0 =
+                             640, at most 1024; negative: the fill's block structure is kept).  In
+                             HM_FP64 mode this applies to the H-matrix that is factored in place; in
+                             HM_FP32_REFINED mode to the complex64 copy (the FP64 H-matrix is kept). */
 } hm_params;
 
 /* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,

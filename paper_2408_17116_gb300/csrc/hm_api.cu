@@ -149,6 +149,7 @@ void storage(hm_handle_s *h, Block *root_unused, double &words, int &maxk, doubl
     ndense = nlr = 0;
     double ks = 0;
     for (Block *b : h->leaves) {
+        if (b->type == B_DENSE && !b->D) continue;  // merged into a dense block of the factor
         if (b->type == B_DENSE) {
             words += (double)b->nr * b->nc;
             ++ndense;
@@ -189,6 +190,17 @@ void rank_features(hm_handle_s *h, const Block *b, float *f)
     f[5] = (float)(std::max(dt, ds) / std::max(dist, 1e-300) / 4.0);
     f[6] = (float)(h->nc / 10.0);
     f[7] = (float)(-std::log10(h->tol) / 10.0);
+}
+
+// Cluster level from which the factor stores dense blocks: the first level whose clusters
+// hold at most factor_leaf unknowns (0: 640); -1 when factor_leaf is negative.
+static int dense_level(hm_handle_s *h)
+{
+    if (h->prm.factor_leaf < 0) return -1;
+    const int bd = h->prm.factor_leaf > 0 ? h->prm.factor_leaf : 640;
+    int lev = 0;
+    while (h->dof * ((h->nnode + (1 << lev) - 1) >> lev) > bd && (1 << lev) < h->nnode) ++lev;
+    return lev;
 }
 
 // The first diagonal dense leaf of a block tree (the top-left leaf).
@@ -240,6 +252,8 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
                                           ? "formulation HM_PEC_CFIE is not built in this library"
                                           : "formulation HM_DIEL_MULLER is not built in this library"};
         if (p->formulation != HM_PEC_MFIE) throw HmError{HM_ERR_ARG, "unknown formulation"};
+        if (p->factor_leaf > 1024)
+            throw HmError{HM_ERR_ARG, "factor_leaf above 1024 (the dense blocks of the FP32 factor)"};
         if (!(p->trunc_tol >= 0.0) || p->quad_order < 0 || (p->quad_order > 0 && (p->quad_order < 4 || p->quad_order > 36)))
             throw HmError{HM_ERR_ARG, "trunc_tol must be >= 0 and quad_order 0 or 4..36"};
         if (p->precision != HM_FP64 && p->precision != HM_FP32_REFINED) throw HmError{HM_ERR_ARG, "unsupported precision"};
@@ -567,6 +581,8 @@ hm_status hm_factor(hm_handle h)
                     ranks.push_back(b->k);
                 }
             batched_truncate<cf>(h, lr, ranks, h->factor_tol);
+            const int lev = dense_level(h);
+            if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
             if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
                 Block32 *d = first_diagonal_leaf(h->root32);
                 HM_CUDA(cudaMemsetAsync(d->D, 0, sizeof(cf) * d->nr, h->stream));
@@ -587,6 +603,11 @@ hm_status hm_factor(hm_handle h)
         }
         Timer t(h->stream);
         h->dirty64.clear();
+        const int lev = dense_level(h);
+        if (lev >= 0) {
+            coarsen_tree<zc>(h, h->root, lev);
+            rebuild_leaves(h);
+        }
         if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
             Block *d = first_diagonal_leaf(h->root);
             HM_CUDA(cudaMemsetAsync(d->D, 0, sizeof(zc) * d->nr, h->stream));
@@ -868,10 +889,20 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_KCORE_LAUNCHES: *out = h->kcore_n; break;
         case HM_Q_REFINE_RES: *out = h->refine_res; break;
         case HM_Q_STORAGE32: {
+            // the blocks reachable from the factor's root (a coarsened tree detaches the
+            // blocks it merged)
             double w32 = 0;
-            for (Block32 *b : h->blocks32) {
-                if (b->type == B_DENSE) w32 += (double)b->nr * b->nc;
-                if (b->type == B_LR) w32 += (double)b->k * (b->nr + b->nc);
+            std::vector<Block32 *> st;
+            if (h->root32) st.push_back(h->root32);
+            while (!st.empty()) {
+                Block32 *b = st.back();
+                st.pop_back();
+                if (b->type == B_HIER)
+                    for (int i = 0; i < 4; ++i) st.push_back(b->ch[i]);
+                else if (b->type == B_DENSE)
+                    w32 += (double)b->nr * b->nc;
+                else
+                    w32 += (double)b->k * (b->nr + b->nc);
             }
             *out = w32;
             break;

@@ -577,12 +577,71 @@ void free_tree(hm_handle_s *h, std::vector<BlockT<Z> *> &owned)
     owned.clear();
 }
 
+// Write the content of block b (dense leaves copied, low-rank leaves as U V^H) into the
+// dense column-major view D (ld) whose top-left entry is unknown (r0, c0).
+template <class Z>
+static void expand_into(hm_handle_s *h, BlockT<Z> *b, Z *D, int ld, int r0, int c0)
+{
+    Z *dst = D + (size_t)(b->c0 - c0) * ld + (b->r0 - r0);
+    switch (b->type) {
+    case B_DENSE:
+        zcopy2d(h, MVT<Z>{dst, b->nr, b->nc, ld}, MVT<Z>{b->D, b->nr, b->nc, b->nr});
+        break;
+    case B_LR:
+        if (b->k)
+            zgemm<Z>(h, 'N', 'C', b->nr, b->nc, b->k, cmk<Z>(1, 0), b->U, b->nr, b->V, b->nc, cmk<Z>(0, 0), dst, ld);
+        else
+            zgemm<Z>(h, 'N', 'N', b->nr, b->nc, 0, cmk<Z>(0, 0), nullptr, 1, nullptr, 1, cmk<Z>(0, 0), dst, ld);
+        break;
+    case B_HIER:
+        for (int i = 0; i < 4; ++i) expand_into(h, b->ch[i], D, ld, r0, c0);
+        break;
+    }
+}
+
+template <class Z>
+static void release_subtree(hm_handle_s *h, BlockT<Z> *b)
+{
+    if (b->type == B_HIER)
+        for (int i = 0; i < 4; ++i) release_subtree(h, b->ch[i]);
+    if (b->D) dfree(h, b->D);
+    if (b->U) dfree(h, b->U);
+    if (b->V) dfree(h, b->V);
+    b->D = b->U = b->V = nullptr;
+    b->k = 0;
+}
+
+// Coarsening of a block tree for its H-LU: every hierarchical block whose clusters lie on
+// cluster level `level` or deeper becomes one dense block holding the same entries
+// (exact: dense leaves are copied and low-rank leaves expanded).  Blocks on coarser levels
+// keep their format, so every block row of the dense level holds dense blocks or whole
+// low-rank blocks of that level and above, and the partial pivoting of a dense diagonal
+// block stays within its own rows.
+template <class Z>
+void coarsen_tree(hm_handle_s *h, BlockT<Z> *b, int level)
+{
+    if (b->type != B_HIER) return;
+    if (h->clusters[b->t].level >= level) {
+        Z *D = (Z *)dalloc(h, sizeof(Z) * (size_t)b->nr * b->nc);
+        for (int i = 0; i < 4; ++i) expand_into(h, b->ch[i], D, b->nr, b->r0, b->c0);
+        for (int i = 0; i < 4; ++i) {
+            release_subtree(h, b->ch[i]);
+            b->ch[i] = nullptr;
+        }
+        b->type = B_DENSE;
+        b->D = D;
+        return;
+    }
+    for (int i = 0; i < 4; ++i) coarsen_tree(h, b->ch[i], level);
+}
+
 #define HM_INST_HLU(Z)                                                                             \
     template void hlu_factor<Z>(hm_handle_s *, BlockT<Z> *, double);                               \
     template void hsolve<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>);                                   \
     template void hmatvec<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>, MVT<Z>, Z, bool);                 \
     template BlockT<Z> *clone_tree<Z>(hm_handle_s *, Block *, std::vector<BlockT<Z> *> &);         \
-    template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);
+    template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);                         \
+    template void coarsen_tree<Z>(hm_handle_s *, BlockT<Z> *, int);
 HM_INST_HLU(zc)
 HM_INST_HLU(cf)
 template void convert_vec<zc, cf>(hm_handle_s *, const zc *, cf *, size_t);

@@ -240,6 +240,9 @@ template <class C>
 BlockT<C> *clone_tree(hm_handle_s *h, Block *b, std::vector<BlockT<C> *> &owned);
 template <class C>
 void free_tree(hm_handle_s *h, std::vector<BlockT<C> *> &owned);
+// Merge every hierarchical block on cluster level `level` or deeper into one dense block.
+template <class C>
+void coarsen_tree(hm_handle_s *h, BlockT<C> *root, int level);
 // y[i] = (To) x[i] for n complex values
 template <class Ti, class To>
 void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n);

@@ -303,14 +303,134 @@ __global__ void __launch_bounds__(1024) k_getrf(int n, C *A, int lda, int *piv, 
 }
 
 template <class C>
+void ztrsm_lln(hm_handle_s *h, const C *L, int ldl, int n, MVT<C> X);
+
+// Panel of the blocked LU: columns [j0, j0 + nb) of an m x m block (rows j0 .. m), one CTA,
+// partial pivoting over the rows below the diagonal (ties to the lowest row); the row
+// interchanges are applied to the panel's columns only (k_laswp_range does the rest).
+template <class C>
+__global__ void __launch_bounds__(512) k_getf2_panel(int m, C *A, int lda, int j0, int nb, int *piv, int *info)
+{
+    typedef typename CReal<C>::R R;
+    __shared__ R sv[32];
+    __shared__ int si[32];
+    __shared__ int s_p;
+    __shared__ C s_inv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = j0; k < j0 + nb; ++k) {
+        R bv = -1;
+        int bi = 0x7fffffff;
+        for (int i = k + tid; i < m; i += nt) {
+            R v = zabs2(A[(size_t)k * lda + i]);
+            if (v > bv || (v == bv && i < bi)) {
+                bv = v;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            R v2 = __shfl_down_sync(0xffffffff, bv, o);
+            int i2 = __shfl_down_sync(0xffffffff, bi, o);
+            if (v2 > bv || (v2 == bv && i2 < bi)) {
+                bv = v2;
+                bi = i2;
+            }
+        }
+        if ((tid & 31) == 0) {
+            sv[tid >> 5] = bv;
+            si[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            R v = sv[0];
+            int ii = si[0];
+            for (int w = 1; w < (nt + 31) / 32; ++w)
+                if (sv[w] > v || (sv[w] == v && si[w] < ii)) {
+                    v = sv[w];
+                    ii = si[w];
+                }
+            if (ii < k || ii >= m) ii = k;
+            s_p = ii;
+            piv[k] = ii;
+            if (!(v > 0)) {
+                if (*info == 0) *info = k + 1;
+                s_inv = cmk<C>(0, 0);
+            } else {
+                s_inv = zdiv(cmk<C>(1, 0), A[(size_t)k * lda + ii]);
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = j0 + tid; j < j0 + nb; j += nt) {
+                C t = A[(size_t)j * lda + k];
+                A[(size_t)j * lda + k] = A[(size_t)j * lda + p];
+                A[(size_t)j * lda + p] = t;
+            }
+        __syncthreads();
+        const C inv = s_inv;
+        for (int i = k + 1 + tid; i < m; i += nt) A[(size_t)k * lda + i] = zmul(A[(size_t)k * lda + i], inv);
+        __syncthreads();
+        const int rows = m - k - 1, cols = j0 + nb - k - 1;
+        for (int e = tid; e < rows * cols; e += nt) {
+            int i = k + 1 + e % rows, j = k + 1 + e / rows;
+            A[(size_t)j * lda + i] = zsub(A[(size_t)j * lda + i], zmul(A[(size_t)k * lda + i], A[(size_t)j * lda + k]));
+        }
+        __syncthreads();
+    }
+}
+
+// Row interchanges k <-> piv[k], k in [k0, k1), on the columns [0, c_lo) and [c_hi, n).
+template <class C>
+__global__ void k_laswp_range(C *A, int lda, int c_lo, int c_hi, int n, const int *piv, int k0, int k1)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = t < c_lo ? t : c_hi + (t - c_lo);
+    if (j >= n) return;
+    C *x = A + (size_t)j * lda;
+    for (int k = k0; k < k1; ++k) {
+        int p = piv[k];
+        if (p != k) {
+            C tmp = x[k];
+            x[k] = x[p];
+            x[p] = tmp;
+        }
+    }
+}
+
+#define LU_NB 32
+
+template <class C>
 void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
 {
     if (n <= 0) return;
-    int T = n >= 512 ? 1024 : (n >= 128 ? 512 : 256);
-    k_getrf<C><<<1, T, 0, h->stream>>>(n, A, lda, piv, d_info);
-    HM_CHECK_LAUNCH();
-    count_launch(h);
     h->flops_factor += 8.0 / 3.0 * n * (double)n * n;
+    if (n <= 256) {
+        int T = n >= 128 ? 512 : 256;
+        k_getrf<C><<<1, T, 0, h->stream>>>(n, A, lda, piv, d_info);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+        return;
+    }
+    // blocked right-looking LU (the same partial pivoting over the whole block): panel,
+    // interchanges on the other columns, U12 = L11^-1 A12, A22 -= L21 U12
+    const double saved = h->flops_factor;
+    for (int j0 = 0; j0 < n; j0 += LU_NB) {
+        const int nb = std::min(LU_NB, n - j0), rest = n - j0 - nb;
+        k_getf2_panel<C><<<1, 512, 0, h->stream>>>(n, A, lda, j0, nb, piv, d_info);
+        HM_CHECK_LAUNCH();
+        const int ncols = j0 + rest;
+        if (ncols > 0) {
+            k_laswp_range<C><<<(ncols + 127) / 128, 128, 0, h->stream>>>(A, lda, j0, j0 + nb, n, piv, j0, j0 + nb);
+            HM_CHECK_LAUNCH();
+        }
+        count_launch(h, ncols > 0 ? 2 : 1);
+        if (rest > 0) {
+            ztrsm_lln<C>(h, A + (size_t)j0 * lda + j0, lda, nb, MVT<C>{A + (size_t)(j0 + nb) * lda + j0, nb, rest, lda});
+            zgemm<C>(h, 'N', 'N', rest, rest, nb, cmk<C>(-1, 0), A + (size_t)j0 * lda + j0 + nb, lda,
+                     A + (size_t)(j0 + nb) * lda + j0, lda, cmk<C>(1, 0), A + (size_t)(j0 + nb) * lda + j0 + nb, lda);
+        }
+    }
+    h->flops_factor = saved;  // counted once above
 }
 
 // ---------------------------------------------------------------------------

@@ -28,6 +28,7 @@
 #define TL_NRB 4   // right-hand sides per pass
 #define TL_KC 128  // rank columns per pass of a low-rank piece
 #define TL_JC 256  // columns of a dense piece staged per pass
+#define TL_ROWS_MAX 1024  // largest row tile (a diagonal block of the tree)
 
 template <class C>
 struct TPiece {
@@ -52,6 +53,25 @@ __device__ __forceinline__ void tile_gemv(const C *__restrict__ A, int ld, int r
                                           C *acc)
 {
     const int tid = threadIdx.x;
+    if (rows > TL_T) {
+        // tiles taller than the CTA: each thread owns rows tid, tid + TL_T, ...
+        for (int r = tid; r < rows; r += TL_T) {
+            C a[TL_NRB];
+#pragma unroll
+            for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
+            for (int j = 0; j < n; ++j) {
+                C v = A[(size_t)j * ld + r];
+#pragma unroll
+                for (int c = 0; c < TL_NRB; ++c)
+                    if (c < nrb) a[c] = zfma(v, zs[j * TL_NRB + c], a[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < TL_NRB; ++c)
+                if (c < nrb) acc[r * TL_NRB + c] = zadd(acc[r * TL_NRB + c], a[c]);
+        }
+        __syncthreads();
+        return;
+    }
     const int G = max(1, TL_T / rows);
     const int r = tid % rows, g = tid / rows;
     C a[TL_NRB];
@@ -82,7 +102,8 @@ __global__ void __launch_bounds__(TL_T) k_tile_partial(const TPiece<C> *__restri
                                                          const TChunk *__restrict__ chunks, const C *__restrict__ X,
                                                          int ldx, int nrhs, C *__restrict__ part, int rmax)
 {
-    __shared__ C acc[TL_T * TL_NRB];
+    extern __shared__ __align__(16) unsigned char tp_raw[];
+    C *acc = (C *)tp_raw;  // [rmax][TL_NRB]
     __shared__ C zs[(TL_JC > TL_KC ? TL_JC : TL_KC) * TL_NRB];
     const TChunk ch = chunks[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -225,6 +246,18 @@ static void identity_fill(hm_handle_s *h, C *I, int n)
     count_launch(h);
 }
 
+// Dynamic shared memory of k_tile_partial (the accumulators of one tile); raises the
+// kernel's limit when a tile needs more than the default 48 KB.
+template <class C>
+static size_t partial_smem(int rmax)
+{
+    const size_t bytes = sizeof(C) * (size_t)std::max(rmax, 1) * TL_NRB;
+    const size_t stat = sizeof(C) * (TL_JC > TL_KC ? TL_JC : TL_KC) * TL_NRB;
+    if (bytes + stat > 48 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(k_tile_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return bytes;
+}
+
 template <class C>
 struct TileOp {
     int N = 0, ntile = 0, rmax = 0;
@@ -308,7 +341,8 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
         int pos = 0;
         for (BlockT<C> *d : diag) {
             if (d->r0 != pos) throw HmError{HM_ERR_STATE, "tile plan: diagonal leaves do not partition the unknowns"};
-            if (d->nr > TL_T) throw HmError{HM_ERR_ARG, "tile plan: a leaf cluster has more than 256 unknowns"};
+            if (d->nr > TL_ROWS_MAX)
+                throw HmError{HM_ERR_ARG, "tile plan: a diagonal block has more than 1024 unknowns"};
             T->r0.push_back(d->r0);
             T->rows.push_back(d->nr);
             T->rmax = std::max(T->rmax, d->nr);
@@ -446,8 +480,9 @@ void tile_matvec(hm_handle_s *h, TileOp<C> *T, const C *X, C *Y, int nrhs, C alp
 {
     if (nrhs <= 0 || T->ntile == 0) return;
     C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->nca, 1) * nrhs * T->rmax);
+    const size_t smem = partial_smem<C>(T->rmax);
     if (T->nca) {
-        k_tile_partial<C><<<T->nca, TL_T, 0, h->stream>>>(T->d_pa, T->d_ca, X, T->N, nrhs, part, T->rmax);
+        k_tile_partial<C><<<T->nca, TL_T, smem, h->stream>>>(T->d_pa, T->d_ca, X, T->N, nrhs, part, T->rmax);
         HM_CHECK_LAUNCH();
     }
     k_tile_reduce<C><<<T->ntile, TL_T, 0, h->stream>>>(T->d_tr0, T->d_trows, T->d_ts0, T->d_ts1, part, nrhs,
@@ -465,12 +500,16 @@ void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
     if (nrhs <= 0 || T->ntile == 0) return;
     C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->maxchunks, 1) * nrhs * T->rmax);
     const size_t smem = sizeof(C) * (size_t)T->rmax * TL_NRB;
+    const size_t psmem = partial_smem<C>(T->rmax);
     for (int i = 0; i < T->ntile; ++i) {
         const int nch = T->cl1[i] - T->cl0[i];
         if (nch) {
-            k_tile_partial<C><<<nch, TL_T, 0, h->stream>>>(T->d_pl, T->d_cl + T->cl0[i], X, T->N, nrhs, part, T->rmax);
+            k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(T->d_pl, T->d_cl + T->cl0[i], X, T->N, nrhs, part,
+                                                               T->rmax);
             HM_CHECK_LAUNCH();
         }
+        if (i == 0 && smem > 48 * 1024)
+            HM_CUDA(cudaFuncSetAttribute(k_tile_finish<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const C *Li = T->d_inv + T->inv_off[i];
         k_tile_finish<C><<<1, TL_T, smem, h->stream>>>(T->r0[i], T->rows[i], nch, part, nrhs, T->rmax, T->piv[i], Li,
                                                        X, T->N);
@@ -480,7 +519,8 @@ void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
     for (int i = T->ntile - 1; i >= 0; --i) {
         const int nch = T->cu1[i] - T->cu0[i];
         if (nch) {
-            k_tile_partial<C><<<nch, TL_T, 0, h->stream>>>(T->d_pu, T->d_cu + T->cu0[i], X, T->N, nrhs, part, T->rmax);
+            k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(T->d_pu, T->d_cu + T->cu0[i], X, T->N, nrhs, part,
+                                                               T->rmax);
             HM_CHECK_LAUNCH();
         }
         const C *Ui = T->d_inv + T->inv_off[i] + (size_t)T->rows[i] * T->rows[i];

@@ -10,9 +10,10 @@ would run for hours on a workstation; zgesv computes the same factorisation
 (partial pivoting; the oracle's LU is checked against it in the oracle pins).
 
 Also written: <name>_x.json with the residual of the stored solution against the
-oracle's matrix, the bound sqrt(|A|_1 |A|_inf) >= |A|_2 (which turns a solution
-error into a bound on the full residual: |A x - b| <= |A|_2 |x - x_o| + |A x_o - b|),
-and the wall times of the fill and of the solve on this machine.
+oracle's matrix, the bound sqrt(|A|_1 |A|_inf) >= |A|_2 and the power-iteration value of
+|A|_2 (either turns a solution error into a bound on the full residual:
+|A x - b| <= |A|_2 |x - x_o| + |A x_o - b|), and the wall times of the fill and of the
+solve on this machine.
 
   python tests/golden/make_dense_solution.py sphere_d8_m4_nc10
 """
@@ -44,9 +45,24 @@ def main(name):
     res = [float(np.linalg.norm(A @ X[r] - b[r]) / np.linalg.norm(b[r])) for r in range(b.shape[0])]
     a1 = float(np.abs(A).sum(axis=0).max())
     ainf = float(np.abs(A).sum(axis=1).max())
+    # the largest singular value by power iteration on A^H A (seeded start vector), run
+    # until the estimate changes by less than 1e-9 relative
+    v = np.random.default_rng(1).standard_normal(o.N) + 0j
+    v /= np.linalg.norm(v)
+    smax = 0.0
+    for it in range(500):
+        w = np.conj(A.T @ np.conj(A @ v))  # A^H (A v) without forming A^H
+        s_new = float(np.sqrt(np.linalg.norm(w)))
+        v = w / np.linalg.norm(w)
+        if abs(s_new - smax) <= 1e-9 * s_new:
+            smax = s_new
+            break
+        smax = s_new
+    power_iters = it + 1
     np.save(os.path.join(HERE, name + "_x.npy"), np.ascontiguousarray(X.astype(np.complex128)))
     meta = {"workload": name, "unknowns": int(o.N), "rhs": int(b.shape[0]), "residual": res,
-            "norm2_bound": float(np.sqrt(a1 * ainf)), "bnorm": [float(np.linalg.norm(b[r])) for r in range(b.shape[0])],
+            "norm2_bound": float(np.sqrt(a1 * ainf)), "norm2_power": smax, "power_iters": power_iters,
+            "bnorm": [float(np.linalg.norm(b[r])) for r in range(b.shape[0])],
             "fill_s": t_fill, "solve_s": t_solve, "host_threads": os.cpu_count(),
             "script": "tests/golden/make_dense_solution.py"}
     with open(os.path.join(HERE, name + "_x.json"), "w") as f:
