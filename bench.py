@@ -343,7 +343,8 @@ def main():
     ms, value = aggregate(ms, N, dist, device="cuda")
     stats = {k.lower(): s.hm_query(k) for k in ("CR", "MAX_RANK", "MEAN_RANK", "LR_BLOCKS", "DENSE_BLOCKS",
                                                  "NEAR_PAIRS", "ACA_NONCONV", "FLOPS_FACTOR", "REFINE_ITERS",
-                                                 "REFINE_RES", "STORAGE", "STORAGE32")}
+                                                 "REFINE_RES", "STORAGE", "STORAGE32", "DENSE_LEVEL",
+                                                 "TRUNC_BATCHES", "TRUNC_JOBS", "TRUNC_MAXK")}
     # e2e: host buffers in and out, wall clock around the public API calls
     e2e_s = None
     if not args.no_e2e:

@@ -89,11 +89,15 @@ typedef struct {
                              H-LU (0 = aca_tol) */
     int quad_order;       /* Gauss points per direction of the self/near rule's inner panels and Duffy squares
                              (0 = 24; 4..36; the outer panels take ceil(2 quad_order / 3)) */
-    int factor_leaf;      /* the H-LU stores, as one dense block each, the hierarchical blocks of the
-                             first cluster level whose clusters hold at most factor_leaf unknowns (0 =
-                             640, at most 1024; negative: the fill's block structure is kept).  In
-                             HM_FP64 mode this applies to the H-matrix that is factored in place; in
-                             HM_FP32_REFINED mode to the complex64 copy (the FP64 H-matrix is kept). */
+    int factor_leaf;      /* the H-LU stores, as one dense block each (an exact merge), the hierarchical
+                             blocks of one cluster level and of every level below it: > 0, the first
+                             level whose clusters hold at most factor_leaf unknowns (at most 4096 for
+                             HM_FP32_REFINED, 2048 for HM_FP64); 0, the coarsest level of clusters of
+                             at most 4096 (complex64) / 640 (complex128) unknowns whose non-low-rank
+                             blocks store at least half of their dense size, else the level of
+                             640-unknown clusters; negative, the fill's block structure.  HM_FP64:
+                             applies to the H-matrix factored in place; HM_FP32_REFINED: to the
+                             complex64 copy (the FP64 H-matrix is kept). */
 } hm_params;
 
 /* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,
@@ -151,7 +155,8 @@ enum {
     HM_Q_KQR_LAUNCHES = 36,
     HM_Q_KCORE_SECONDS = 37,  /* core factorisation: pivoted QR (complex64) or Jacobi SVD (complex128) */
     HM_Q_KCORE_FLOPS = 38,    /* counted for the pivoted QR only (the Jacobi sweep count varies) */
-    HM_Q_KCORE_LAUNCHES = 39
+    HM_Q_KCORE_LAUNCHES = 39,
+    HM_Q_DENSE_LEVEL = 40  /* cluster level from which the last hm_factor stored dense blocks (-1: none) */
 };
 
 const char *hm_version(void);

@@ -192,15 +192,24 @@ void rank_features(hm_handle_s *h, const Block *b, float *f)
     f[7] = (float)(-std::log10(h->tol) / 10.0);
 }
 
-// Cluster level from which the factor stores dense blocks: the first level whose clusters
-// hold at most factor_leaf unknowns (0: 640); -1 when factor_leaf is negative.
-static int dense_level(hm_handle_s *h)
+// Cluster level from which the factor stores dense blocks.  factor_leaf > 0: the first
+// level whose clusters hold at most factor_leaf unknowns.  factor_leaf = 0: the coarsest
+// level of clusters of at most `cap` unknowns (4,096 for the complex64 factor, 640 for the
+// complex128 one) whose non-low-rank blocks store at least half of their dense size in
+// H-format, else the level of 640-unknown clusters.  -1 when factor_leaf is negative.
+template <class Z>
+static int dense_level(hm_handle_s *h, BlockT<Z> *root)
 {
     if (h->prm.factor_leaf < 0) return -1;
-    const int bd = h->prm.factor_leaf > 0 ? h->prm.factor_leaf : 640;
-    int lev = 0;
-    while (h->dof * ((h->nnode + (1 << lev) - 1) >> lev) > bd && (1 << lev) < h->nnode) ++lev;
-    return lev;
+    auto level_of = [&](int bd) {
+        int lev = 0;
+        while (h->dof * ((h->nnode + (1 << lev) - 1) >> lev) > bd && (1 << lev) < h->nnode) ++lev;
+        return lev;
+    };
+    if (h->prm.factor_leaf > 0) return level_of(h->prm.factor_leaf);
+    const int cap = sizeof(Z) == sizeof(cf) ? 4096 : 640;
+    const int L = dense_level_by_storage<Z>(h, root, cap, 0.5);
+    return L >= 0 ? L : level_of(640);
 }
 
 // The first diagonal dense leaf of a block tree (the top-left leaf).
@@ -252,8 +261,8 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
                                           ? "formulation HM_PEC_CFIE is not built in this library"
                                           : "formulation HM_DIEL_MULLER is not built in this library"};
         if (p->formulation != HM_PEC_MFIE) throw HmError{HM_ERR_ARG, "unknown formulation"};
-        if (p->factor_leaf > 1024)
-            throw HmError{HM_ERR_ARG, "factor_leaf above 1024 (the dense blocks of the FP32 factor)"};
+        if (p->factor_leaf > (p->precision == HM_FP32_REFINED ? 4096 : 2048))
+            throw HmError{HM_ERR_ARG, "factor_leaf above 4096 (complex64 factor) or 2048 (complex128)"};
         if (!(p->trunc_tol >= 0.0) || p->quad_order < 0 || (p->quad_order > 0 && (p->quad_order < 4 || p->quad_order > 36)))
             throw HmError{HM_ERR_ARG, "trunc_tol must be >= 0 and quad_order 0 or 4..36"};
         if (p->precision != HM_FP64 && p->precision != HM_FP32_REFINED) throw HmError{HM_ERR_ARG, "unsupported precision"};
@@ -581,8 +590,9 @@ hm_status hm_factor(hm_handle h)
                     ranks.push_back(b->k);
                 }
             batched_truncate<cf>(h, lr, ranks, h->factor_tol);
-            const int lev = dense_level(h);
+            const int lev = dense_level<cf>(h, h->root32);
             if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
+            h->dense_lev = lev;
             if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
                 Block32 *d = first_diagonal_leaf(h->root32);
                 HM_CUDA(cudaMemsetAsync(d->D, 0, sizeof(cf) * d->nr, h->stream));
@@ -603,11 +613,12 @@ hm_status hm_factor(hm_handle h)
         }
         Timer t(h->stream);
         h->dirty64.clear();
-        const int lev = dense_level(h);
+        const int lev = dense_level<zc>(h, h->root);
         if (lev >= 0) {
             coarsen_tree<zc>(h, h->root, lev);
             rebuild_leaves(h);
         }
+        h->dense_lev = lev;
         if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
             Block *d = first_diagonal_leaf(h->root);
             HM_CUDA(cudaMemsetAsync(d->D, 0, sizeof(zc) * d->nr, h->stream));
@@ -888,6 +899,7 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_KCORE_FLOPS: *out = h->kcore_flops; break;
         case HM_Q_KCORE_LAUNCHES: *out = h->kcore_n; break;
         case HM_Q_REFINE_RES: *out = h->refine_res; break;
+        case HM_Q_DENSE_LEVEL: *out = h->dense_lev; break;
         case HM_Q_STORAGE32: {
             // the blocks reachable from the factor's root (a coarsened tree detaches the
             // blocks it merged)

@@ -437,7 +437,7 @@ static void trsm_U_right_block(hm_handle_s *h, BlockT<Z> *U, BlockT<Z> *B)
         return;
     }
     if (B->type == B_DENSE) {
-        if (U->type == B_DENSE) {
+        if (U->type == B_DENSE && U->nr <= 256) {  // row-parallel solve; larger blocks go through U^-H B^H
             ztrsm_run(h, U->D, U->nr, U->nr, MVT<Z>{B->D, B->nr, B->nc, B->nr});
             return;
         }
@@ -635,13 +635,55 @@ void coarsen_tree(hm_handle_s *h, BlockT<Z> *b, int level)
     for (int i = 0; i < 4; ++i) coarsen_tree(h, b->ch[i], level);
 }
 
+template <class Z>
+static double subtree_words(const BlockT<Z> *b)
+{
+    if (b->type == B_DENSE) return (double)b->nr * b->nc;
+    if (b->type == B_LR) return (double)b->k * (b->nr + b->nc);
+    double s = 0;
+    for (int i = 0; i < 4; ++i) s += subtree_words(b->ch[i]);
+    return s;
+}
+
+template <class Z>
+static void level_words(hm_handle_s *h, const BlockT<Z> *b, std::vector<double> &hw, std::vector<double> &dw)
+{
+    if (b->type == B_LR) return;  // low-rank blocks keep their format at every level
+    const int L = h->clusters[b->t].level;
+    if ((int)hw.size() <= L) {
+        hw.resize(L + 1, 0.0);
+        dw.resize(L + 1, 0.0);
+    }
+    hw[L] += subtree_words(b);
+    dw[L] += (double)b->nr * b->nc;
+    if (b->type == B_HIER)
+        for (int i = 0; i < 4; ++i) level_words(h, b->ch[i], hw, dw);
+}
+
+// The coarsest cluster level whose clusters hold at most `cap` unknowns and whose
+// non-low-rank blocks (the ones a merge turns dense) store, in H-format, at least `theta`
+// of their dense size: merging there costs little memory and removes the formatted
+// arithmetic below it.  -1 when no level qualifies.
+template <class Z>
+int dense_level_by_storage(hm_handle_s *h, BlockT<Z> *root, int cap, double theta)
+{
+    std::vector<double> hw, dw;
+    level_words(h, root, hw, dw);
+    for (int L = 0; L < (int)hw.size(); ++L) {
+        if (h->dof * ((h->nnode + (1 << L) - 1) >> L) > cap) continue;
+        if (dw[L] > 0 && hw[L] >= theta * dw[L]) return L;
+    }
+    return -1;
+}
+
 #define HM_INST_HLU(Z)                                                                             \
     template void hlu_factor<Z>(hm_handle_s *, BlockT<Z> *, double);                               \
     template void hsolve<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>);                                   \
     template void hmatvec<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>, MVT<Z>, Z, bool);                 \
     template BlockT<Z> *clone_tree<Z>(hm_handle_s *, Block *, std::vector<BlockT<Z> *> &);         \
     template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);                         \
-    template void coarsen_tree<Z>(hm_handle_s *, BlockT<Z> *, int);
+    template void coarsen_tree<Z>(hm_handle_s *, BlockT<Z> *, int);                                \
+    template int dense_level_by_storage<Z>(hm_handle_s *, BlockT<Z> *, int, double);
 HM_INST_HLU(zc)
 HM_INST_HLU(cf)
 template void convert_vec<zc, cf>(hm_handle_s *, const zc *, cf *, size_t);

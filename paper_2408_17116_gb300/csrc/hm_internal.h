@@ -149,6 +149,7 @@ struct hm_handle_s {
     double cur_tol = 1e-7;       // truncation tolerance of the factorisation in progress
     int fault = 0;               // host-side fault injection armed by hm_inject_fault (HM_FAULT_*)
     int *d_info_cur = nullptr;   // zero-pivot flag of the H-LU in progress (device), else null
+    int dense_lev = -1;          // cluster level from which the last factor stored dense blocks
     // block-row plans (hm_tiles.cu): product with the FP64 H-matrix, sweeps of the factors
     TileOp<zc> *tmat64 = nullptr, *tmatcopy = nullptr, *tfac64 = nullptr;
     TileOp<cf> *tfac32 = nullptr;
@@ -243,6 +244,10 @@ void free_tree(hm_handle_s *h, std::vector<BlockT<C> *> &owned);
 // Merge every hierarchical block on cluster level `level` or deeper into one dense block.
 template <class C>
 void coarsen_tree(hm_handle_s *h, BlockT<C> *root, int level);
+// Coarsest level of clusters of at most cap unknowns whose non-low-rank blocks store at
+// least theta of their dense size (-1: none).
+template <class C>
+int dense_level_by_storage(hm_handle_s *h, BlockT<C> *root, int cap, double theta);
 // y[i] = (To) x[i] for n complex values
 template <class Ti, class To>
 void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n);

@@ -1049,6 +1049,15 @@ __global__ void __launch_bounds__(QR_T) k_qrcp(const QRCPDesc<C> *__restrict__ d
 // Truncated recompression of U V^H (batched): QR of both factors, SVD of the core
 // R_U R_V^H, keep the smallest rank k' with sqrt(sum_{i>k'} s_i^2) <= tol |s|_2.
 // ---------------------------------------------------------------------------
+// Core factorisation of a truncation: column-pivoted QR stopped at the tolerance (the
+// complex64 factor, and every recompression inside an H-LU) or one-sided Jacobi SVD (the
+// recompression of the complex128 H-matrix after ACA).
+template <class C>
+static bool use_qrcp(const hm_handle_s *h)
+{
+    return std::is_same<C, cf>::value || h->d_info_cur != nullptr;
+}
+
 template <class C>
 struct TruncJob {
     typedef typename CReal<C>::R R;
@@ -1069,7 +1078,7 @@ template <class C>
 static void trunc_stage1(hm_handle_s *h, std::vector<TruncJob<C>> &jobs)
 {
     typedef typename CReal<C>::R R;
-    const bool qrcp = std::is_same<C, cf>::value;
+    const bool qrcp = use_qrcp<C>(h);
     // workspace and copies
     std::vector<QRJob<C>> qd;
     for (auto &J : jobs) {
@@ -1237,7 +1246,7 @@ static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector
     typedef typename CReal<C>::R R;
     S.resize(jobs.size());
     ord.resize(jobs.size());
-    if (std::is_same<C, cf>::value) {
+    if (use_qrcp<C>(h)) {
         // QRCP: only the chosen ranks come back (ord[i][0])
         std::vector<int> rk(jobs.size());
         for (size_t i = 0; i < jobs.size(); ++i)
@@ -1287,8 +1296,8 @@ int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const 
     std::vector<std::vector<int>> ord;
     fetch_sv(h, jobs, S, ord);
     account_kernels(h);
-    if (std::is_same<C, cf>::value) h->kcore_flops += householder_flops(jobs[0].r1, jobs[0].r2, ord[0][0]);
-    if (std::is_same<C, cf>::value) return trunc_stage2_qrcp(h, jobs[0], std::min(ord[0][0], kmax > 0 ? kmax : K), Uo, Vo);
+    if (use_qrcp<C>(h)) h->kcore_flops += householder_flops(jobs[0].r1, jobs[0].r2, ord[0][0]);
+    if (use_qrcp<C>(h)) return trunc_stage2_qrcp(h, jobs[0], std::min(ord[0][0], kmax > 0 ? kmax : K), Uo, Vo);
     return trunc_stage2(h, jobs[0], S[0], ord[0], tol, Uo, Vo);
 }
 
@@ -1339,12 +1348,12 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
         std::vector<std::vector<int>> ord;
         fetch_sv(h, jobs, S, ord);
         account_kernels(h);
-        if (std::is_same<C, cf>::value)
+        if (use_qrcp<C>(h))
             for (size_t t = 0; t < jobs.size(); ++t) h->kcore_flops += householder_flops(jobs[t].r1, jobs[t].r2, ord[t][0]);
         for (size_t t = 0; t < jobs.size(); ++t) {
             BlockT<C> *b = blks[idx[t]];
             C *Uo, *Vo;
-            int kk = std::is_same<C, cf>::value ? trunc_stage2_qrcp(h, jobs[t], ord[t][0], &Uo, &Vo)
+            int kk = use_qrcp<C>(h) ? trunc_stage2_qrcp(h, jobs[t], ord[t][0], &Uo, &Vo)
                                                 : trunc_stage2(h, jobs[t], S[t], ord[t], tol, &Uo, &Vo);
             dfree(h, b->U);
             dfree(h, b->V);

@@ -14,9 +14,11 @@
 // recursion subtracts, level by level, L21 X1 from X2 before the permutation of a
 // diagonal leaf is applied to its own rows, so every tile receives exactly the sum of its
 // block row's left leaves times the final values of their columns.  Here each step of a
-// sweep is two launches: one CTA per chunk of the tile's pieces writes a partial sum, and
-// one CTA subtracts the partials in a fixed order, applies the pivots and multiplies by
-// the explicit inverse of the diagonal factor (computed once after the factorisation).
+// sweep has one CTA per chunk of the tile's pieces writing a partial sum; the partials are
+// then subtracted in a fixed order, the pivots applied and the result multiplied by
+// the explicit inverse of the diagonal factor (computed once after the factorisation):
+// a gather of the subtracted right-hand side by the block's pivot permutation, then a
+// product with the inverse over CTAs of 256 rows (three launches per step).
 // The product is one launch over every chunk of every tile plus one reduction launch.
 // Summation order is fixed, so results are deterministic.
 #include <algorithm>
@@ -28,7 +30,11 @@
 #define TL_NRB 4   // right-hand sides per pass
 #define TL_KC 128  // rank columns per pass of a low-rank piece
 #define TL_JC 256  // columns of a dense piece staged per pass
-#define TL_ROWS_MAX 1024  // largest row tile (a diagonal block of the tree)
+// largest row tile (a diagonal block of the tree): the tile's accumulators of
+// k_tile_partial live in shared memory
+template <class C> struct TileRows;
+template <> struct TileRows<cf> { static constexpr int value = 4096; };
+template <> struct TileRows<zc> { static constexpr int value = 2048; };
 
 template <class C>
 struct TPiece {
@@ -181,52 +187,53 @@ __global__ void k_tile_reduce(const int *__restrict__ tr0, const int *__restrict
     }
 }
 
-// Sweep step finish (one CTA): z = X[r0 .. r0 + rows, :] - sum_{s < nslots} part[s] (fixed
-// order); forward: z = P z (the diagonal leaf's pivots, applied in order); then
-// X[r0 .., :] = Minv z with Minv the explicit inverse of the tile's triangular factor.
+// Sweep step, part 1 (CTAs over the tile's rows): z[j][c] = X[r0 + g(j), c] - sum_s
+// part[s][c][g(j)] in a fixed order, g = the diagonal block's row permutation (the pivots
+// applied in order; the identity for the backward sweep).  z: [nrhs][rows].
 template <class C>
-__global__ void __launch_bounds__(TL_T) k_tile_finish(int r0, int rows, int nslots, const C *__restrict__ part,
-                                                        int nrhs, int rmax, const int *__restrict__ piv,
-                                                        const C *__restrict__ Minv, C *X, int ldx)
+__global__ void k_tile_prep(int r0, int rows, int nslots, const C *__restrict__ part, int nrhs, int rmax,
+                            const int *__restrict__ gperm, const C *__restrict__ X, int ldx, C *__restrict__ z)
 {
-    extern __shared__ __align__(16) unsigned char tf_raw[];
-    C *z = (C *)tf_raw;  // [rows][TL_NRB]
-    const int tid = threadIdx.x;
+    const size_t n = (size_t)rows * nrhs;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / rows), j = (int)(e - (size_t)c * rows);
+        const int g = gperm ? gperm[j] : j;
+        C s = X[(size_t)c * ldx + r0 + g];
+        for (int q = 0; q < nslots; ++q) s = zsub(s, part[((size_t)q * nrhs + c) * rmax + g]);
+        z[(size_t)c * rows + j] = s;
+    }
+}
+
+// Sweep step, part 2 (CTAs over blocks of TL_T rows): X[r0 + i, c] = sum_j Minv[i][j] z[j][c],
+// Minv the explicit inverse of the diagonal block's triangular factor (column-major).
+template <class C>
+__global__ void __launch_bounds__(TL_T) k_tile_mul(int r0, int rows, int nrhs, const C *__restrict__ Minv,
+                                                     const C *__restrict__ z, C *X, int ldx)
+{
+    __shared__ C zs[TL_T * TL_NRB];
+    const int i = blockIdx.x * TL_T + threadIdx.x;
     for (int cb = 0; cb < nrhs; cb += TL_NRB) {
         const int nrb = min(TL_NRB, nrhs - cb);
-        for (int e = tid; e < rows * TL_NRB; e += TL_T) {
-            int i = e / TL_NRB, c = e - i * TL_NRB;
-            C s = cmk<C>(0, 0);
-            if (c < nrb) {
-                s = X[(size_t)(cb + c) * ldx + r0 + i];
-                for (int q = 0; q < nslots; ++q) s = zsub(s, part[((size_t)q * nrhs + cb + c) * rmax + i]);
-            }
-            z[e] = s;
-        }
-        __syncthreads();
-        if (piv && tid < nrb) {
-            for (int k = 0; k < rows; ++k) {
-                int p = piv[k];
-                if (p != k) {
-                    C tmp = z[k * TL_NRB + tid];
-                    z[k * TL_NRB + tid] = z[p * TL_NRB + tid];
-                    z[p * TL_NRB + tid] = tmp;
-                }
-            }
-        }
-        __syncthreads();
         C a[TL_NRB];
-        for (int e = tid; e < rows; e += TL_T) {
 #pragma unroll
-            for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
-            for (int j = 0; j < rows; ++j) {
-                C m = Minv[(size_t)j * rows + e];
-#pragma unroll
-                for (int c = 0; c < TL_NRB; ++c) a[c] = zfma(m, z[j * TL_NRB + c], a[c]);
+        for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
+        for (int j0 = 0; j0 < rows; j0 += TL_T) {
+            const int nj = min(TL_T, rows - j0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < nj * TL_NRB; e += TL_T) {
+                int j = e / TL_NRB, c = e - j * TL_NRB;
+                zs[e] = c < nrb ? z[(size_t)(cb + c) * rows + j0 + j] : cmk<C>(0, 0);
             }
-            for (int c = 0; c < nrb; ++c) X[(size_t)(cb + c) * ldx + r0 + e] = a[c];
+            __syncthreads();
+            if (i < rows)
+                for (int j = 0; j < nj; ++j) {
+                    C m = Minv[(size_t)(j0 + j) * rows + i];
+#pragma unroll
+                    for (int c = 0; c < TL_NRB; ++c) a[c] = zfma(m, zs[j * TL_NRB + c], a[c]);
+                }
         }
-        __syncthreads();
+        if (i < rows)
+            for (int c = 0; c < nrb; ++c) X[(size_t)(cb + c) * ldx + r0 + i] = a[c];
     }
 }
 
@@ -275,7 +282,7 @@ struct TileOp {
     int maxchunks = 0;
     C *d_inv = nullptr;                   // per tile: L^-1 then U^-1 (rows x rows each)
     std::vector<size_t> inv_off;
-    std::vector<const int *> piv;         // per tile: the diagonal leaf's pivots (device)
+    std::vector<const int *> gperm;       // per tile: row permutation of its pivots (device)
     std::vector<void *> owned;
 };
 
@@ -341,8 +348,9 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
         int pos = 0;
         for (BlockT<C> *d : diag) {
             if (d->r0 != pos) throw HmError{HM_ERR_STATE, "tile plan: diagonal leaves do not partition the unknowns"};
-            if (d->nr > TL_ROWS_MAX)
-                throw HmError{HM_ERR_ARG, "tile plan: a diagonal block has more than 1024 unknowns"};
+            if (d->nr > TileRows<C>::value)
+                throw HmError{HM_ERR_ARG, "tile plan: a diagonal block has more than " +
+                                              std::to_string(TileRows<C>::value) + " unknowns"};
             T->r0.push_back(d->r0);
             T->rows.push_back(d->nr);
             T->rmax = std::max(T->rmax, d->nr);
@@ -456,8 +464,27 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                 identity_fill(h, Ui, n);
                 ztrsm_lln(h, diag[i]->D, n, n, MVT<C>{Li, n, n, n});
                 ztrsm_lun(h, diag[i]->D, n, n, MVT<C>{Ui, n, n, n});
-                T->piv.push_back(diag[i]->piv);
             }
+            // the pivots of each diagonal block as one gather: applying the interchanges
+            // k <-> piv[k] in order to z is z_new[j] = z_old[g[j]]
+            std::vector<int> gall;
+            std::vector<size_t> goff;
+            for (int i = 0; i < T->ntile; ++i) {
+                const int n = T->rows[i];
+                std::vector<int> pv(n), g(n);
+                HM_CUDA(cudaMemcpyAsync(pv.data(), diag[i]->piv, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
+                HM_CUDA(cudaStreamSynchronize(h->stream));
+                for (int k = 0; k < n; ++k) g[k] = k;
+                for (int k = 0; k < n; ++k) {
+                    const int q = pv[k];
+                    if (q < 0 || q >= n) throw HmError{HM_ERR_NUMERIC, "tile plan: pivot index out of range"};
+                    std::swap(g[k], g[q]);
+                }
+                goff.push_back(gall.size());
+                gall.insert(gall.end(), g.begin(), g.end());
+            }
+            const int *d_g = upload(h, gall, T->owned);
+            for (int i = 0; i < T->ntile; ++i) T->gperm.push_back(d_g + goff[i]);
         }
     } catch (...) {
         tile_free(h, T);
@@ -499,37 +526,28 @@ void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
     if (!T->factored) throw HmError{HM_ERR_STATE, "tile_solve on an unfactored plan"};
     if (nrhs <= 0 || T->ntile == 0) return;
     C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->maxchunks, 1) * nrhs * T->rmax);
-    const size_t smem = sizeof(C) * (size_t)T->rmax * TL_NRB;
+    C *z = (C *)dalloc(h, sizeof(C) * (size_t)T->rmax * nrhs);
     const size_t psmem = partial_smem<C>(T->rmax);
-    for (int i = 0; i < T->ntile; ++i) {
-        const int nch = T->cl1[i] - T->cl0[i];
+    auto step = [&](int i, const TPiece<C> *pcs, const TChunk *chs, int nch, const int *g, const C *Minv) {
         if (nch) {
-            k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(T->d_pl, T->d_cl + T->cl0[i], X, T->N, nrhs, part,
-                                                               T->rmax);
+            k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(pcs, chs, X, T->N, nrhs, part, T->rmax);
             HM_CHECK_LAUNCH();
         }
-        if (i == 0 && smem > 48 * 1024)
-            HM_CUDA(cudaFuncSetAttribute(k_tile_finish<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const C *Li = T->d_inv + T->inv_off[i];
-        k_tile_finish<C><<<1, TL_T, smem, h->stream>>>(T->r0[i], T->rows[i], nch, part, nrhs, T->rmax, T->piv[i], Li,
-                                                       X, T->N);
+        const int rows = T->rows[i];
+        const int gp = std::min(64, (int)((rows * (size_t)nrhs + TL_T - 1) / TL_T));
+        k_tile_prep<C><<<std::max(gp, 1), TL_T, 0, h->stream>>>(T->r0[i], rows, nch, part, nrhs, T->rmax, g, X, T->N, z);
         HM_CHECK_LAUNCH();
-        count_launch(h, nch ? 2 : 1);
-    }
-    for (int i = T->ntile - 1; i >= 0; --i) {
-        const int nch = T->cu1[i] - T->cu0[i];
-        if (nch) {
-            k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(T->d_pu, T->d_cu + T->cu0[i], X, T->N, nrhs, part,
-                                                               T->rmax);
-            HM_CHECK_LAUNCH();
-        }
-        const C *Ui = T->d_inv + T->inv_off[i] + (size_t)T->rows[i] * T->rows[i];
-        k_tile_finish<C><<<1, TL_T, smem, h->stream>>>(T->r0[i], T->rows[i], nch, part, nrhs, T->rmax, nullptr, Ui,
-                                                       X, T->N);
+        k_tile_mul<C><<<(rows + TL_T - 1) / TL_T, TL_T, 0, h->stream>>>(T->r0[i], rows, nrhs, Minv, z, X, T->N);
         HM_CHECK_LAUNCH();
-        count_launch(h, nch ? 2 : 1);
-    }
+        count_launch(h, nch ? 3 : 2);
+    };
+    for (int i = 0; i < T->ntile; ++i)
+        step(i, T->d_pl, T->d_cl + T->cl0[i], T->cl1[i] - T->cl0[i], T->gperm[i], T->d_inv + T->inv_off[i]);
+    for (int i = T->ntile - 1; i >= 0; --i)
+        step(i, T->d_pu, T->d_cu + T->cu0[i], T->cu1[i] - T->cu0[i], nullptr,
+             T->d_inv + T->inv_off[i] + (size_t)T->rows[i] * T->rows[i]);
     dfree(h, part);
+    dfree(h, z);
 }
 
 #define HM_INST_TILES(Z)                                                              \
