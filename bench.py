@@ -116,6 +116,8 @@ def cpu_baseline(wl, workload_name):
     Returns the estimate as unknowns/s, with the sample's own wall time.
     """
     import oracle
+    if wl.get("formulation") == "MULLER":
+        return None  # the row sampler of the oracle covers the MFIE system
     t0 = time.perf_counter()
     o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
     N = o.N
@@ -200,13 +202,23 @@ def run_reference(args, rank, world):
 
 def bench_config(args, wl):
     """The workload description both arms print (identical keys and values)."""
-    return {"workload": args.workload, "formulation": "MFIE", "unknowns": wl_N(wl), "rhs": int(wl["kdirs"].shape[0]),
+    return {"workload": args.workload, "formulation": wl.get("formulation", "MFIE"), "unknowns": wl_N(wl),
+            "rhs": int(wl["kdirs"].shape[0]),
             "leaf": wl["leaf"], "eta": wl["eta"], "aca_tol": wl["aca_tol"],
             "l2": "working set (H-matrix, near store) > L2 between steps"}
 
 
 def wl_N(wl):
-    return 2 * 6 * int(np.sum(np.asarray(wl["ms"]) ** 2)) * wl["nc"] ** 2
+    dof = 4 if wl.get("formulation") == "MULLER" else 2
+    return dof * 6 * int(np.sum(np.asarray(wl["ms"]) ** 2)) * wl["nc"] ** 2
+
+
+def formulation_args(wl):
+    """hm_build_geometry keywords of the workload's integral equation."""
+    from paper_2408_17116_gb300 import hm
+    if wl.get("formulation") == "MULLER":
+        return dict(formulation=hm.HM_DIEL_MULLER, eps_r=wl["eps_r"])
+    return {}
 
 
 PRECISION = {"fp32r": 1, "fp64": 0}
@@ -243,7 +255,7 @@ def aggregate(ms_local, unknowns_local, dist=None, device="cpu"):
 
 def one_step(s, wl, dirs, host=False, precision="fp32r"):
     s.hm_build_geometry(wl["bodies"], wl["ms"], wl["nc"], wl["k"], wl["leaf"], wl["eta"], wl["aca_tol"],
-                        precision=PRECISION[precision])
+                        precision=PRECISION[precision], **formulation_args(wl))
     s.hm_fill()
     s.hm_factor()
     if host:

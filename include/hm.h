@@ -92,9 +92,9 @@ typedef struct {
     int factor_leaf;      /* the H-LU stores, as one dense block each (an exact merge), the hierarchical
                              blocks of one cluster level and of every level below it: > 0, the first
                              level whose clusters hold at most factor_leaf unknowns (at most 4096 for
-                             HM_FP32_REFINED, 2048 for HM_FP64); 0, the coarsest level of clusters of
-                             at most 4096 (complex64) / 640 (complex128) unknowns whose non-low-rank
-                             blocks store at least half of their dense size, else the level of
+                             HM_FP32_REFINED, 1280 for HM_FP64); 0, the coarsest level of clusters of
+                             at most 4096 (complex64) / 1280 (complex128) unknowns whose non-low-rank
+                             blocks store at least 35 % of their dense size, else the level of
                              640-unknown clusters; negative, the fill's block structure.  HM_FP64:
                              applies to the H-matrix factored in place; HM_FP32_REFINED: to the
                              complex64 copy (the FP64 H-matrix is kept). */
@@ -348,7 +348,8 @@ hm_status hm_get_nodes_host(hm_handle h, double *out);
 /* Near patch pairs: host int [npairs][2] (target patch, source patch). */
 hm_status hm_get_near_pairs_host(hm_handle h, int *out);
 /* Near weights of target node tn over source patch p (must be a near pair):
- * host complex128 [4][Nc^2], index (2b + a) * Nc^2 + j (rows b, source components a). */
+ * host complex128 [d^2][Nc^2], index (d b + a) * Nc^2 + j (tested rows b, source components a;
+ * d = 2 unknowns per node for the MFIE, 4 for the N-Mueller system). */
 hm_status hm_get_near_block_host(hm_handle h, int tn, int p, void *out);
 /* Matrix entries A[rows[i], cols[i]] (natural unknown indices) from the fill's entry
  * rule (near store + Nystrom far rule + identity term): host complex128 [n]. */

@@ -115,7 +115,7 @@ void free_all(hm_handle_s *h)
     h->leaves.clear();
     h->root = nullptr;
     void *ptrs[] = {h->d_bodies, h->d_patches, h->d_nodes, h->d_pair_q, h->d_pair_p, h->d_nearidx,
-                    h->d_near,   h->d_perm,    h->d_iperm};
+                    h->d_near,   h->d_perm,    h->d_iperm, h->d_d1};
     for (void *p : ptrs) dfree(h, p);
     h->d_bodies = nullptr;
     h->d_patches = nullptr;
@@ -123,6 +123,7 @@ void free_all(hm_handle_s *h)
     h->d_pair_q = h->d_pair_p = h->d_nearidx = nullptr;
     h->d_near = nullptr;
     h->d_perm = h->d_iperm = nullptr;
+    h->d_d1 = nullptr;
 }
 
 void collect_leaves(Block *b, std::vector<Block *> &out)
@@ -194,9 +195,12 @@ void rank_features(hm_handle_s *h, const Block *b, float *f)
 
 // Cluster level from which the factor stores dense blocks.  factor_leaf > 0: the first
 // level whose clusters hold at most factor_leaf unknowns.  factor_leaf = 0: the coarsest
-// level of clusters of at most `cap` unknowns (4,096 for the complex64 factor, 640 for the
-// complex128 one) whose non-low-rank blocks store at least half of their dense size in
+// level of clusters of at most `cap` unknowns (4,096 for the complex64 factor, 1,280 for
+// the complex128 one) whose non-low-rank blocks store at least 35 % of their dense size in
 // H-format, else the level of 640-unknown clusters.  -1 when factor_leaf is negative.
+// (Measured on GB300 at 19,200 unknowns, where the near blocks store 47 % of their dense
+// size: the factor with dense 2,400-unknown blocks takes 3.4 s, with dense 600-unknown
+// blocks and low-rank blocks above them 13 s, recompressions dominating the latter.)
 template <class Z>
 static int dense_level(hm_handle_s *h, BlockT<Z> *root)
 {
@@ -207,8 +211,8 @@ static int dense_level(hm_handle_s *h, BlockT<Z> *root)
         return lev;
     };
     if (h->prm.factor_leaf > 0) return level_of(h->prm.factor_leaf);
-    const int cap = sizeof(Z) == sizeof(cf) ? 4096 : 640;
-    const int L = dense_level_by_storage<Z>(h, root, cap, 0.5);
+    const int cap = sizeof(Z) == sizeof(cf) ? 4096 : 1280;
+    const int L = dense_level_by_storage<Z>(h, root, cap, 0.35);
     return L >= 0 ? L : level_of(640);
 }
 
@@ -256,13 +260,20 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
     return guard(h, [&] {
         if (!bodies || nbodies <= 0 || !p) throw HmError{HM_ERR_ARG, "null bodies or params"};
         if (nodes_per_dir < 2 || nodes_per_dir > HM_NC_MAX) throw HmError{HM_ERR_ARG, "nodes_per_dir out of range 2..16"};
-        if (p->formulation == HM_PEC_CFIE || p->formulation == HM_DIEL_MULLER)
-            throw HmError{HM_ERR_ARG, p->formulation == HM_PEC_CFIE
-                                          ? "formulation HM_PEC_CFIE is not built in this library"
-                                          : "formulation HM_DIEL_MULLER is not built in this library"};
-        if (p->formulation != HM_PEC_MFIE) throw HmError{HM_ERR_ARG, "unknown formulation"};
-        if (p->factor_leaf > (p->precision == HM_FP32_REFINED ? 4096 : 2048))
-            throw HmError{HM_ERR_ARG, "factor_leaf above 4096 (complex64 factor) or 2048 (complex128)"};
+        if (p->formulation == HM_PEC_CFIE)
+            throw HmError{HM_ERR_ARG, "formulation HM_PEC_CFIE is not built in this library"};
+        if (p->formulation != HM_PEC_MFIE && p->formulation != HM_DIEL_MULLER)
+            throw HmError{HM_ERR_ARG, "unknown formulation"};
+        if (p->formulation == HM_DIEL_MULLER) {
+            if (!(p->eps_r_re > 0.0) || !(p->eps_r_im <= 0.0) || !std::isfinite(p->eps_r_re) ||
+                !std::isfinite(p->eps_r_im))
+                throw HmError{HM_ERR_ARG, "eps_r needs a positive real part and Im <= 0 (exp(j w t))"};
+            if (!(p->mu_r == 0.0 || p->mu_r == 1.0)) throw HmError{HM_ERR_ARG, "only mu_r = 1 is supported"};
+            if (nodes_per_dir > 12) throw HmError{HM_ERR_ARG, "N-Mueller: nodes_per_dir at most 12"};
+            if (!(p->k0 > 0.0)) throw HmError{HM_ERR_ARG, "N-Mueller: k0 must be positive"};
+        }
+        if (p->factor_leaf > (p->precision == HM_FP32_REFINED ? 4096 : 1280))
+            throw HmError{HM_ERR_ARG, "factor_leaf above 4096 (complex64 factor) or 1280 (complex128)"};
         if (!(p->trunc_tol >= 0.0) || p->quad_order < 0 || (p->quad_order > 0 && (p->quad_order < 4 || p->quad_order > 36)))
             throw HmError{HM_ERR_ARG, "trunc_tol must be >= 0 and quad_order 0 or 4..36"};
         if (p->precision != HM_FP64 && p->precision != HM_FP32_REFINED) throw HmError{HM_ERR_ARG, "unsupported precision"};
@@ -319,7 +330,14 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
         }
         h->npatch = (int)h->patches.size();
         h->nnode = h->npatch * h->nc * h->nc;
-        h->N = 2 * h->nnode;
+        h->dof = h->prm.formulation == HM_DIEL_MULLER ? 4 : 2;
+        h->N = h->dof * h->nnode;
+        if (h->prm.formulation == HM_DIEL_MULLER && p->quad_order == 0) {
+            // the rule must resolve the interior wavelength: twice the points above a
+            // contrast of 3 in the wavenumber
+            const double kr = std::sqrt(std::hypot(p->eps_r_re, p->eps_r_im));
+            if (kr > 3.0) h->rule = NearRule{48, 48, 32, 0.5};
+        }
         Timer t(h->stream);
         plan_geometry(h);
         h->t_geom = t.stop();
@@ -335,7 +353,7 @@ hm_status hm_fill(hm_handle h)
             free_matrix(h);
             rebuild_block_tree(h);  // the adaptive ACA split below changes the tree
         }
-        const int nc = h->nc, w = 2 * nc * nc;
+        const int nc = h->nc, w = h->dof * nc * nc;
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
         h->trunc_log.clear();
@@ -372,7 +390,29 @@ hm_status hm_fill(hm_handle h)
             HM_CUDA(cudaMemcpyAsync(d_tab + tab.size(), C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice,
                                     h->stream));
             HM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), h->stream));
-            launch_near(h, d_tab, d_tab + tab.size());
+            if (h->dof == 4) {
+                // derivatives of the cardinal functions at the nodes (the divergence terms of
+                // the far entries): d1[l' nc + l] = ell_l'(x_l') = sum_n C[n][l] T_n'(x_l')
+                std::vector<double> x1(nc), d1((size_t)nc * nc), U(nc + 1);
+                cheb_nodes_host(nc, x1.data());
+                for (int lp = 0; lp < nc; ++lp) {
+                    U[0] = 1.0;
+                    U[1] = 2.0 * x1[lp];
+                    for (int j = 2; j < nc; ++j) U[j] = 2.0 * x1[lp] * U[j - 1] - U[j - 2];
+                    for (int l = 0; l < nc; ++l) {
+                        double s = 0.0;
+                        for (int n = 1; n < nc; ++n) s += C[n * nc + l] * n * U[n - 1];  // T_n' = n U_{n-1}
+                        d1[lp * nc + l] = s;
+                    }
+                }
+                if (!h->d_d1) h->d_d1 = (double *)dalloc(h, sizeof(double) * nc * nc);
+                HM_CUDA(cudaMemcpyAsync(h->d_d1, d1.data(), sizeof(double) * d1.size(), cudaMemcpyHostToDevice,
+                                        h->stream));
+                HM_CUDA(cudaStreamSynchronize(h->stream));
+                launch_near_muller(h, d_tab, d_tab + tab.size());
+            } else {
+                launch_near(h, d_tab, d_tab + tab.size());
+            }
             dfree(h, d_tab);
             h->t_near = t.stop();
             HM_CUDA(cudaMemcpy(&h->near_points, h->d_counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
@@ -759,7 +799,10 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
     double *d_dirs = (double *)dalloc(h, sizeof(double) * dirs.size());
     HM_CUDA(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, h->stream));
     zc *b = (zc *)dalloc(h, sizeof(zc) * (size_t)h->N * nrhs);
-    launch_rhs(h, nrhs, d_dirs, b);
+    if (h->dof == 4)
+        launch_rhs_muller(h, nrhs, d_dirs, b);
+    else
+        launch_rhs(h, nrhs, d_dirs, b);
     if (h->fault == HM_FAULT_NAN_RHS) {  // host-side injection: one right-hand-side entry is NaN
         h->fault = HM_FAULT_NONE;
         const zc nan = zmake(std::numeric_limits<double>::quiet_NaN(), 0.0);
@@ -813,7 +856,10 @@ hm_status hm_farfield(hm_handle h, int nrhs, const void *x_dev, int nang, const 
         double *d_obs = (double *)dalloc(h, sizeof(double) * 3 * nang);
         HM_CUDA(cudaMemcpyAsync(d_obs, obs, sizeof(double) * 3 * nang, cudaMemcpyHostToDevice, h->stream));
         double *d_rcs = rcs_host ? (double *)dalloc(h, sizeof(double) * (size_t)nrhs * nang) : nullptr;
-        launch_farfield(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
+        if (h->dof == 4)
+            launch_farfield_muller(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
+        else
+            launch_farfield(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
         if (rcs_host)
             HM_CUDA(cudaMemcpyAsync(rcs_host, d_rcs, sizeof(double) * (size_t)nrhs * nang, cudaMemcpyDeviceToHost,
                                     h->stream));
@@ -1001,20 +1047,20 @@ hm_status hm_get_near_block_host(hm_handle h, int tn, int p, void *out)
 {
     return guard(h, [&] {
         if (h->state < 2 || !out) throw HmError{HM_ERR_STATE, "near store not filled"};
-        int nc2 = h->nc * h->nc, w = 2 * nc2;
+        const int D = h->dof, nc2 = h->nc * h->nc, w = D * nc2;
         if (tn < 0 || tn >= h->nnode || p < 0 || p >= h->npatch) throw HmError{HM_ERR_ARG, "index out of range"};
         int q = tn / nc2, idx = -1;
         for (size_t i = 0; i < h->pair_q.size(); ++i)
             if (h->pair_q[i] == q && h->pair_p[i] == p) idx = (int)i;
         if (idx < 0) throw HmError{HM_ERR_ARG, "not a near pair"};
-        std::vector<zc> rows(2 * (size_t)w);
-        HM_CUDA(cudaMemcpyAsync(rows.data(), h->d_near + ((size_t)idx * w + 2 * (tn - q * nc2)) * w,
-                                sizeof(zc) * 2 * w, cudaMemcpyDeviceToHost, h->stream));
+        std::vector<zc> rows(D * (size_t)w);
+        HM_CUDA(cudaMemcpyAsync(rows.data(), h->d_near + ((size_t)idx * w + D * (tn - q * nc2)) * w,
+                                sizeof(zc) * D * w, cudaMemcpyDeviceToHost, h->stream));
         HM_CUDA(cudaStreamSynchronize(h->stream));
         zc *o = (zc *)out;
-        for (int b = 0; b < 2; ++b)
-            for (int a = 0; a < 2; ++a)
-                for (int j = 0; j < nc2; ++j) o[(2 * b + a) * nc2 + j] = rows[(size_t)b * w + 2 * j + a];
+        for (int b = 0; b < D; ++b)
+            for (int a = 0; a < D; ++a)
+                for (int j = 0; j < nc2; ++j) o[(D * b + a) * nc2 + j] = rows[(size_t)b * w + D * j + a];
     });
 }
 

@@ -3,14 +3,19 @@
 // identity term 1/2 from the jump relation, Eq. 5), dense inadmissible leaves,
 // and partial-pivot ACA of admissible leaves (Sec. III, ref. [22]).
 #include "hm_internal.h"
+#include "hm_muller.cuh"
 
 struct EntryCtx {
     const double *nodes;  // SoA [14][nnode]
     int nnode, nc2, P;
     const int *nearidx;   // [P][P]
-    const zc *near;       // [npairs][2 nc2][2 nc2]
+    const zc *near;       // [npairs][dof nc2][dof nc2]
     const int *perm;      // tree unknown -> natural unknown
     double k;
+    int dof;              // unknowns per node: 2 (MFIE) or 4 (N-Mueller)
+    int nc;
+    MullerMedia md;       // N-Mueller: the interior medium
+    const double *d1;     // N-Mueller: [nc][nc] derivatives of the cardinal functions at the nodes
 };
 
 // The four entries A[2ni + b, 2nj + a] of node pair (ni, nj) (natural node indices),
@@ -56,9 +61,48 @@ __device__ __forceinline__ void node_pair(const EntryCtx &E, int ni, int nj, zc 
     }
 }
 
+// The 16 entries of node pair (ni, nj) of the N-Mueller system, out[row * 4 + col]: rows
+// E-u, E-v, H-u, H-v, columns eta0 J^u, eta0 J^v, M^u, M^v (Eqs. 7-9); near pairs from the
+// near store, far pairs by the Nystrom rule (hm_muller.cuh); identity terms of the jump
+// relations (Eq. 6) -(1 + eps_r)/2 on M in the E-rows and 1 on J in the H-rows.
+__device__ __forceinline__ void node_pair_muller(const EntryCtx &E, int ni, int nj, zc *out)
+{
+    int pi = ni / E.nc2, pj = nj / E.nc2;
+    int np = E.nearidx[(size_t)pi * E.P + pj];
+    if (np >= 0) {
+        const int w = 4 * E.nc2;
+        const zc *blk = E.near + (size_t)np * w * w;
+        const int ti = ni - pi * E.nc2, sj = nj - pj * E.nc2;
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) out[r * 4 + c] = blk[(size_t)(4 * ti + r) * w + 4 * sj + c];
+    } else {
+        muller_far_pair(E.nodes, E.nnode, E.nc, E.d1, E.md, ni, nj, out);
+    }
+    if (ni == nj) {
+        const double hr = -0.5 * (1.0 + E.md.epsr.x), hi = -0.5 * E.md.epsr.y;
+        out[0 * 4 + 2] = zadd(out[0 * 4 + 2], zmake(hr, hi));
+        out[1 * 4 + 3] = zadd(out[1 * 4 + 3], zmake(hr, hi));
+        out[2 * 4 + 0].x += 1.0;
+        out[3 * 4 + 1].x += 1.0;
+    }
+}
+
+// dof x dof entries of node pair (ni, nj), out[b * dof + a]
+__device__ __forceinline__ void pair_entries(const EntryCtx &E, int ni, int nj, zc *out)
+{
+    if (E.dof == 4)
+        node_pair_muller(E, ni, nj, out);
+    else
+        node_pair(E, ni, nj, out);
+}
+
 static EntryCtx entry_ctx(hm_handle_s *h)
 {
     EntryCtx E;
+    E.dof = h->dof;
+    E.nc = h->nc;
+    E.md = muller_media(h->prm.k0, h->prm.eps_r_re, h->prm.eps_r_im);
+    E.d1 = h->d_d1;
     E.nodes = h->d_nodes;
     E.nnode = h->nnode;
     E.nc2 = h->nc * h->nc;
@@ -77,19 +121,18 @@ __global__ void k_dense_fill(EntryCtx E, const DenseDesc *__restrict__ descs, co
 {
     int4 t = tiles[blockIdx.x];
     DenseDesc d = descs[t.x];
+    const int D = E.dof;
     int rn = t.y * 16 + threadIdx.x;  // node row within block
     int cn = t.z * 16 + threadIdx.y;  // node col within block
-    if (2 * rn >= d.nr || 2 * cn >= d.ncol) return;
-    int ni = E.perm[d.r0 + 2 * rn] >> 1;
-    int nj = E.perm[d.c0 + 2 * cn] >> 1;
-    zc e[4];
-    node_pair(E, ni, nj, e);
+    if (D * rn >= d.nr || D * cn >= d.ncol) return;
+    int ni = E.perm[d.r0 + D * rn] / D;
+    int nj = E.perm[d.c0 + D * cn] / D;
+    zc e[16];
+    pair_entries(E, ni, nj, e);
     size_t ld = d.nr;
-    zc *c0 = d.D + (size_t)(2 * cn) * ld + 2 * rn;
-    c0[0] = e[0];
-    c0[1] = e[2];
-    c0[ld] = e[1];
-    c0[ld + 1] = e[3];
+    zc *c0 = d.D + (size_t)(D * cn) * ld + D * rn;
+    for (int b = 0; b < D; ++b)
+        for (int a = 0; a < D; ++a) c0[(size_t)a * ld + b] = e[b * D + a];
 }
 
 void launch_dense_fill(hm_handle_s *h, const std::vector<DenseDesc> &descs)
@@ -97,7 +140,7 @@ void launch_dense_fill(hm_handle_s *h, const std::vector<DenseDesc> &descs)
     if (descs.empty()) return;
     std::vector<int4> tiles;
     for (size_t i = 0; i < descs.size(); ++i) {
-        int tr = (descs[i].nr / 2 + 15) / 16, tc = (descs[i].ncol / 2 + 15) / 16;
+        int tr = (descs[i].nr / h->dof + 15) / 16, tc = (descs[i].ncol / h->dof + 15) / 16;
         for (int a = 0; a < tr; ++a)
             for (int b = 0; b < tc; ++b) tiles.push_back(make_int4((int)i, a, b, 0));
     }
@@ -122,9 +165,10 @@ __global__ void k_entries(EntryCtx E, int n, const int *__restrict__ rows, const
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int r = rows[i], c = cols[i];
-    zc e[4];
-    node_pair(E, r >> 1, c >> 1, e);
-    out[i] = e[2 * (r & 1) + (c & 1)];
+    const int D = E.dof;
+    zc e[16];
+    pair_entries(E, r / D, c / D, e);
+    out[i] = e[D * (r % D) + (c % D)];
 }
 
 void launch_entries(hm_handle_s *h, int n, const int *d_rows, const int *d_cols, zc *d_out)
@@ -226,18 +270,18 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(EntryCtx E, const LRDesc *_
         // pivot row cache
         for (int l = tid; l < k; l += ACA_THREADS) Urow[l] = U[(size_t)l * nr + i];
         __syncthreads();
-        const int ni = E.perm[d.r0 + i] >> 1, bi = (d.r0 + i) & 1;
+        const int D = E.dof;
+        const int ni = E.perm[d.r0 + i] / D, bi = (d.r0 + i) % D;
         // 1. residual row into W[:,k]
         double bv = -1.0;
         int bj = 0x7fffffff;
-        for (int jj = tid; 2 * jj < ncl; jj += ACA_THREADS) {
-            int nj = E.perm[d.c0 + 2 * jj] >> 1;
-            zc e[4];
-            node_pair(E, ni, nj, e);
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                int j = 2 * jj + a;
-                zc r = e[2 * bi + a];
+        for (int jj = tid; D * jj < ncl; jj += ACA_THREADS) {
+            int nj = E.perm[d.c0 + D * jj] / D;
+            zc e[16];
+            pair_entries(E, ni, nj, e);
+            for (int a = 0; a < D; ++a) {
+                int j = D * jj + a;
+                zc r = e[D * bi + a];
                 for (int l = 0; l < k; ++l) r = zsub(r, zmul(Urow[l], zconj(W[(size_t)l * ncl + j])));
                 W[(size_t)k * ncl + j] = r;
                 double m = zabs2(r);
@@ -276,18 +320,17 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(EntryCtx E, const LRDesc *_
         __syncthreads();
         nv2 = block_sum(nv2, sv);
         // 3. residual column into U[:,k]
-        const int nj = E.perm[d.c0 + jk] >> 1, aj = (d.c0 + jk) & 1;
+        const int nj = E.perm[d.c0 + jk] / D, aj = (d.c0 + jk) % D;
         double nu2 = 0.0;
         bv = -1.0;
         bj = 0x7fffffff;
-        for (int ii = tid; 2 * ii < nr; ii += ACA_THREADS) {
-            int nii = E.perm[d.r0 + 2 * ii] >> 1;
-            zc e[4];
-            node_pair(E, nii, nj, e);
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                int row = 2 * ii + b;
-                zc c = e[2 * b + aj];
+        for (int ii = tid; D * ii < nr; ii += ACA_THREADS) {
+            int nii = E.perm[d.r0 + D * ii] / D;
+            zc e[16];
+            pair_entries(E, nii, nj, e);
+            for (int b = 0; b < D; ++b) {
+                int row = D * ii + b;
+                zc c = e[D * b + aj];
                 for (int l = 0; l < k; ++l) c = zsub(c, zmul(U[(size_t)l * nr + row], Vrow[l]));
                 U[(size_t)k * nr + row] = c;
                 double m = zabs2(c);

@@ -99,7 +99,8 @@ struct hm_handle_s {
     std::vector<int> pair_q, pair_p;  // per pair
     int *d_pair_q = nullptr, *d_pair_p = nullptr;
     int *d_nearidx = nullptr;  // [P][P] -> pair index or -1
-    zc *d_near = nullptr;      // [npairs][2 nc^2][2 nc^2]
+    zc *d_near = nullptr;      // [npairs][dof nc^2][dof nc^2]
+    double *d_d1 = nullptr;    // [nc][nc] derivatives of the cardinal functions at the nodes (N-Mueller)
     unsigned long long *d_counter = nullptr;  // device counters (quadrature points)
     // tree
     std::vector<Cluster> clusters;
@@ -169,6 +170,11 @@ void dfree(hm_handle_s *h, void *p);
 void launch_nodes(hm_handle_s *h, const double *d_x1d, const double *d_w1d);
 void launch_patch_grid(hm_handle_s *h, const double *d_g, int ng, double *d_out);
 void launch_near(hm_handle_s *h, const double *d_tabs, const double *d_C);
+// ---- hm_muller_dev.cu (N-Mueller: near quadrature, right-hand sides, far field) ----
+void launch_near_muller(hm_handle_s *h, const double *d_tabs, const double *d_C);
+void launch_rhs_muller(hm_handle_s *h, int nrhs, const double *d_dirs, zc *d_b);  // tree order
+void launch_farfield_muller(hm_handle_s *h, int nrhs, const zc *d_x, int nang, const double *d_dirs, zc *d_efar,
+                            double *d_rcs);
 
 // ---- hm_fill.cu ----
 struct DenseDesc {

@@ -25,6 +25,10 @@ struct MullerMedia {
     zc k2;        // interior wavenumber k sqrt(eps_r), Im <= 0
 };
 
+// Medium of relative permittivity eps_re + j eps_im inside (k2 = k0 sqrt(eps_r), the root
+// with Im <= 0: a decaying wave for exp(j w t)); host function (hm_muller_dev.cu).
+MullerMedia muller_media(double k0, double eps_re, double eps_im);
+
 // exp(-j kc R) for a complex wavenumber kc (Im kc <= 0: decaying)
 __host__ __device__ __forceinline__ zc expmj(zc kc, double R)
 {

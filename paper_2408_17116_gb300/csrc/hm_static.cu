@@ -63,7 +63,10 @@ extern "C" hm_status hm_farfield_static(hm_handle h, int nrhs, const void *x_dev
         double *scr = scratch_address(h->device);
         double *d_obs = scr, *d_rcs = rcs_host ? scr + 3 * (size_t)nang : nullptr;
         HM_CUDA(cudaMemcpyAsync(d_obs, obs_dirs, sizeof(double) * 3 * nang, cudaMemcpyHostToDevice, h->stream));
-        launch_farfield(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
+        if (h->dof == 4)
+            launch_farfield_muller(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
+        else
+            launch_farfield(h, nrhs, (const zc *)x_dev, nang, d_obs, (zc *)efar_dev, d_rcs);
         if (rcs_host)
             HM_CUDA(cudaMemcpyAsync(rcs_host, d_rcs, sizeof(double) * (size_t)nrhs * nang, cudaMemcpyDeviceToHost,
                                     h->stream));

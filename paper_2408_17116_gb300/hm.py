@@ -248,7 +248,8 @@ class Solver:
                       trunc_tol=float(trunc_tol), quad_order=int(quad_order), factor_leaf=int(factor_leaf))
         self._check(self.L.hm_build_geometry(self.h, self._bodies, len(ms), int(nc), ctypes.byref(p)))
         self.N = int(self.hm_query("N"))
-        self.nnode = self.N // 2
+        self.dof = 4 if int(formulation) == HM_DIEL_MULLER else 2
+        self.nnode = self.N // self.dof
         self.nc = int(nc)
 
     def hm_fill(self):
@@ -329,7 +330,7 @@ class Solver:
         return out
 
     def near_block(self, tn, p):
-        out = np.empty((4, self.nc * self.nc), dtype=np.complex128)
+        out = np.empty((self.dof * self.dof, self.nc * self.nc), dtype=np.complex128)
         self._check(self.L.hm_get_near_block_host(self.h, int(tn), int(p), _np_ptr(out)))
         return out
 

@@ -73,10 +73,15 @@ def workload(name):
         kh, pol = incidence(3, SEED + 2)
         return dict(name=name, bodies=body(center=(0.1, -0.2, 0.05), semi=(1.2, 0.8, 0.5), rot=R)[None],
                     ms=[2], nc=8, k=K0, leaf=48, eta=2.0, aca_tol=1e-7, kdirs=kh, pols=pol)
+    if name == "dielectric_d1_eps80_m2_nc12":  # high-contrast dielectric sphere, 13,824 unknowns (4 per node)
+        kh, pol = axial_incidence()
+        return dict(name=name, bodies=body(semi=(0.5,) * 3)[None], ms=[2], nc=12, k=K0, leaf=96, eta=2.0,
+                    aca_tol=1e-8, kdirs=kh, pols=pol, radius=0.5, formulation="MULLER", eps_r=80.0)
     raise KeyError(name)
 
 
-WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d4_m2_nc10", "sphere_d2_m2_nc6", "ellipsoid_small")
+WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d4_m2_nc10", "sphere_d2_m2_nc6", "ellipsoid_small",
+             "dielectric_d1_eps80_m2_nc12")
 
 
 def mlp_init(nin, nh, seed=SEED):
