@@ -156,7 +156,12 @@ enum {
     HM_Q_KCORE_SECONDS = 37,  /* core factorisation: pivoted QR (complex64) or Jacobi SVD (complex128) */
     HM_Q_KCORE_FLOPS = 38,    /* counted for the pivoted QR only (the Jacobi sweep count varies) */
     HM_Q_KCORE_LAUNCHES = 39,
-    HM_Q_DENSE_LEVEL = 40  /* cluster level from which the last hm_factor stored dense blocks (-1: none) */
+    HM_Q_DENSE_LEVEL = 40, /* cluster level from which the last hm_factor stored dense blocks (-1: none) */
+    /* products of at least 1e9 real flops in the last hm_factor (the dense Schur updates), device
+     * time from CUDA events around each launch, their algorithmic real flops and count: */
+    HM_Q_KGEMM_SECONDS = 41,
+    HM_Q_KGEMM_FLOPS = 42,
+    HM_Q_KGEMM_LAUNCHES = 43
 };
 
 const char *hm_version(void);

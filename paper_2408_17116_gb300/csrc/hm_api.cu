@@ -613,6 +613,8 @@ hm_status hm_factor(hm_handle h)
         h->tr_batches = h->tr_jobs = h->tr_maxk = h->tr_work = h->tr_seconds = 0;
         h->kqr_s = h->kqr_flops = h->kqr_n = h->kcore_s = h->kcore_flops = h->kcore_n = 0;
         h->trunc_log.clear();
+        gemm_timing_collect(h);
+        h->kgemm_s = h->kgemm_flops = h->kgemm_n = 0;
         if (h->prm.precision == HM_FP32_REFINED) {
             // the FP64 H-matrix stays unfactored: it is the refinement operator
             Timer t(h->stream);
@@ -642,6 +644,7 @@ hm_status hm_factor(hm_handle h)
             h->tfac32 = tile_build<cf>(h, h->root32, true);
             if (!h->tmat64) h->tmat64 = tile_build<zc>(h, h->root, false);
             h->t_factor = t.stop();
+            gemm_timing_collect(h);
             h->state = 3;
             return;
         }
@@ -669,6 +672,7 @@ hm_status hm_factor(hm_handle h)
         tile_free(h, h->tfac64);
         h->tfac64 = tile_build<zc>(h, h->root, true);
         h->t_factor = t.stop();
+        gemm_timing_collect(h);
         h->state = 3;
     });
 }
@@ -946,6 +950,9 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_KCORE_LAUNCHES: *out = h->kcore_n; break;
         case HM_Q_REFINE_RES: *out = h->refine_res; break;
         case HM_Q_DENSE_LEVEL: *out = h->dense_lev; break;
+        case HM_Q_KGEMM_SECONDS: gemm_timing_collect(h); *out = h->kgemm_s; break;
+        case HM_Q_KGEMM_FLOPS: gemm_timing_collect(h); *out = h->kgemm_flops; break;
+        case HM_Q_KGEMM_LAUNCHES: gemm_timing_collect(h); *out = h->kgemm_n; break;
         case HM_Q_STORAGE32: {
             // the blocks reachable from the factor's root (a coarsened tree detaches the
             // blocks it merged)
@@ -1020,6 +1027,11 @@ void hm_destroy(hm_handle h)
     if (h->d_counter) cudaFree(h->d_counter);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (const GemmTiming &t : h->gemm_pending) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    for (cudaEvent_t e : h->gemm_free) cudaEventDestroy(e);
     delete h;
 }
 

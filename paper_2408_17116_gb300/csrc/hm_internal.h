@@ -79,6 +79,12 @@ typedef MVT<zc> MV;
 template <class C>
 struct TileOp;
 
+// A product timed with CUDA events (hm_linalg.cu), read after the next synchronisation.
+struct GemmTiming {
+    cudaEvent_t e0, e1;
+    double flops;
+};
+
 struct hm_handle_s {
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -151,6 +157,10 @@ struct hm_handle_s {
     int fault = 0;               // host-side fault injection armed by hm_inject_fault (HM_FAULT_*)
     int *d_info_cur = nullptr;   // zero-pivot flag of the H-LU in progress (device), else null
     int dense_lev = -1;          // cluster level from which the last factor stored dense blocks
+    // products of at least 1e9 real flops, timed with CUDA events (reset with the statistics)
+    std::vector<GemmTiming> gemm_pending;
+    std::vector<cudaEvent_t> gemm_free;
+    double kgemm_s = 0, kgemm_flops = 0, kgemm_n = 0;
     // block-row plans (hm_tiles.cu): product with the FP64 H-matrix, sweeps of the factors
     TileOp<zc> *tmat64 = nullptr, *tmatcopy = nullptr, *tfac64 = nullptr;
     TileOp<cf> *tfac32 = nullptr;
@@ -191,6 +201,8 @@ void launch_aca(hm_handle_s *h, const std::vector<LRDesc> &descs, int *d_rank, i
 void launch_entries(hm_handle_s *h, int n, const int *d_rows, const int *d_cols, zc *d_out);
 
 // ---- hm_linalg.cu (complex dense kernels, instantiated for complex128 and complex64) ----
+cudaEvent_t gemm_event(hm_handle_s *h);
+void gemm_timing_collect(hm_handle_s *h);
 // C = alpha op(A) op(B) + beta C, op: 'N' or 'C' (conjugate transpose)
 template <class C>
 void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, C alpha, const C *A, int lda, const C *B, int ldb,

@@ -211,10 +211,53 @@ void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, C alpha, con
     } else {
         g.work = nullptr;
         g.kchunk = k;
+        // the large products (at least 1e9 real flops) are timed with CUDA events around
+        // the launch; their durations are read after the factorisation (gemm_timing_collect)
+        const double fl = 8.0 * m * n * k;
+        const bool timed = fl >= 1e9;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            e0 = gemm_event(h);
+            e1 = gemm_event(h);
+            HM_CUDA(cudaEventRecord(e0, h->stream));
+        }
         k_zgemm<C><<<dim3(gm, gn, 1), 256, 0, h->stream>>>(g);
         HM_CHECK_LAUNCH();
+        if (timed) {
+            HM_CUDA(cudaEventRecord(e1, h->stream));
+            h->gemm_pending.push_back(GemmTiming{e0, e1, fl});
+        }
         count_launch(h);
     }
+}
+
+cudaEvent_t gemm_event(hm_handle_s *h)
+{
+    if (h->gemm_free.empty()) {
+        cudaEvent_t e;
+        HM_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    cudaEvent_t e = h->gemm_free.back();
+    h->gemm_free.pop_back();
+    return e;
+}
+
+// Accumulate the device time of the timed products recorded since the last call (the
+// stream must have been synchronised) and return their events to the pool.
+void gemm_timing_collect(hm_handle_s *h)
+{
+    for (const GemmTiming &t : h->gemm_pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+            h->kgemm_s += 1e-3 * ms;
+            h->kgemm_flops += t.flops;
+            h->kgemm_n += 1;
+        }
+        h->gemm_free.push_back(t.e0);
+        h->gemm_free.push_back(t.e1);
+    }
+    h->gemm_pending.clear();
 }
 
 // ---------------------------------------------------------------------------

@@ -21,7 +21,8 @@ Q = dict(N=0, NNODE=1, NPATCH=2, NEAR_PAIRS=3, DENSE_BLOCKS=4, LR_BLOCKS=5, CR=6
          T_RECOMPRESS=21, REFINE_ITERS=22, REFINE_RES=23, STORAGE32=24, ACA_PREALLOC=25, ACA_RERUNS=26,
          RANK_PRED_ERR=27, TRUNC_BATCHES=28, TRUNC_JOBS=29, TRUNC_MAXK=30, TRUNC_WORK=31, T_TRUNC=32,
          ACA_SKIPPED=33, KQR_SECONDS=34, KQR_FLOPS=35, KQR_LAUNCHES=36, KCORE_SECONDS=37,
-         KCORE_FLOPS=38, KCORE_LAUNCHES=39, DENSE_LEVEL=40)
+         KCORE_FLOPS=38, KCORE_LAUNCHES=39, DENSE_LEVEL=40, KGEMM_SECONDS=41, KGEMM_FLOPS=42,
+         KGEMM_LAUNCHES=43)
 RANK_NFEAT = 8
 HM_FP64, HM_FP32_REFINED = 0, 1
 HM_PEC_MFIE, HM_PEC_CFIE, HM_DIEL_MULLER = 0, 1, 2
