@@ -91,13 +91,17 @@ typedef struct {
                              (0 = 24; 4..36; the outer panels take ceil(2 quad_order / 3)) */
     int factor_leaf;      /* the H-LU stores, as one dense block each (an exact merge), the hierarchical
                              blocks of one cluster level and of every level below it: > 0, the first
-                             level whose clusters hold at most factor_leaf unknowns (at most 4096 for
-                             HM_FP32_REFINED, 1280 for HM_FP64); 0, the coarsest level of clusters of
-                             at most 4096 (complex64) / 1280 (complex128) unknowns whose non-low-rank
-                             blocks store at least 35 % of their dense size, else the level of
-                             640-unknown clusters; negative, the fill's block structure.  HM_FP64:
-                             applies to the H-matrix factored in place; HM_FP32_REFINED: to the
-                             complex64 copy (the FP64 H-matrix is kept). */
+                             level whose clusters hold at most factor_leaf unknowns; 0 (adaptive):
+                             HM_FP32_REFINED with tensor-core products, the coarsest level whose merged
+                             storage fits in 40 % of the free device memory (the whole matrix, when it
+                             fits); otherwise the coarsest level of clusters of at most 4096 (complex64)
+                             / 1280 (complex128) unknowns whose non-low-rank blocks store at least 35 %
+                             of their dense size, else the level of 640-unknown clusters; negative, the
+                             fill's block structure.  HM_FP64: applies to the H-matrix factored in
+                             place; HM_FP32_REFINED: to the complex64 copy (the FP64 H-matrix is kept). */
+    int simt_gemm;        /* HM_FP32_REFINED: nonzero keeps every complex64 product of the H-LU on the
+                             CUDA cores; 0 runs the large ones on the tensor cores (tcgen05, operands
+                             split into two BF16 parts, three products accumulated in FP32) */
 } hm_params;
 
 /* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,
@@ -161,7 +165,22 @@ enum {
      * time from CUDA events around each launch, their algorithmic real flops and count: */
     HM_Q_KGEMM_SECONDS = 41,
     HM_Q_KGEMM_FLOPS = 42,
-    HM_Q_KGEMM_LAUNCHES = 43
+    HM_Q_KGEMM_LAUNCHES = 43,
+    /* the same for the tensor-core products (k_tc_gemm) of the last hm_factor, flops counted
+     * as BF16 tensor flops: three split products of 8 m n k each */
+    HM_Q_KTC_SECONDS = 44,
+    HM_Q_KTC_FLOPS = 45,
+    HM_Q_KTC_LAUNCHES = 46,
+    /* device seconds (CUDA events) of phases of the last hm_factor: the column panels of the
+     * blocked dense LU (panel LU, interchanges, updates inside the panel), the row blocks
+     * U12 = L11^-1 A12 with their interchanges, and the block-row plans with the explicit
+     * inverses of the diagonal tiles; of the last hm_solve: the substitution sweeps and the
+     * FP64 H-matrix products of the refinement */
+    HM_Q_T_LU_PANEL = 47,
+    HM_Q_T_LU_U12 = 48,
+    HM_Q_T_TILE_BUILD = 49,
+    HM_Q_T_SOLVE_SWEEP = 50,
+    HM_Q_T_SOLVE_MATVEC = 51
 };
 
 const char *hm_version(void);
@@ -243,6 +262,19 @@ const char *hm_last_error(hm_handle h);
  * (m + n) K^2, device seconds of the QR launch, device seconds of the core launch, host wall
  * seconds of the batch.  Diagnostics for the recompression kernels; synchronises. */
 hm_status hm_get_trunc_log_host(hm_handle h, int *nbatches, double *out);
+
+/* The complex64 GEMM of the FP32 H-LU on caller-owned device memory (Sec. III, Eq. 23: the
+ * Schur-complement products of the factorisation): C = alpha op(A) op(B) + beta C with
+ * op 'N' (as stored) or 'C' (conjugate transpose); A, B, C column-major complex64
+ * (interleaved real/imaginary float pairs) with leading dimensions lda, ldb, ldc; op(A) is
+ * m x k, op(B) k x n.  alpha and beta point at two floats (real, imaginary) on the host.
+ * path 0: the dispatch hm_factor uses (tensor cores for products of at least 2e8 real
+ * flops with m, n >= 64 and k >= 16, unless simt_gemm was set); 1: CUDA cores; 2: tensor
+ * cores (HM_ERR_ARG when m or n < 64 or k < 16).  Runs on the handle's stream and
+ * synchronises it; HM_ERR_TIMEOUT when a bounded pipeline wait of the tensor-core kernel
+ * expired (C is then unspecified).  Any handle state. */
+hm_status hm_cgemm(hm_handle h, char opA, char opB, int m, int n, int k, const float *alpha, const void *A, int lda,
+                   const void *B, int ldb, const float *beta, void *C, int ldc, int path);
 
 /* Host-side fault injection for tests of the error paths (the paper has no counterpart).
  * Arms one fault for the next call that reaches it; no GPU fault, trap or hang is caused.

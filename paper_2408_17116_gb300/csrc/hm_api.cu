@@ -124,6 +124,9 @@ void free_all(hm_handle_s *h)
     h->d_near = nullptr;
     h->d_perm = h->d_iperm = nullptr;
     h->d_d1 = nullptr;
+    dfree(h, h->tc_ws);
+    h->tc_ws = nullptr;
+    h->tc_ws_bytes = 0;
 }
 
 void collect_leaves(Block *b, std::vector<Block *> &out)
@@ -211,6 +214,15 @@ static int dense_level(hm_handle_s *h, BlockT<Z> *root)
         return lev;
     };
     if (h->prm.factor_leaf > 0) return level_of(h->prm.factor_leaf);
+    if (sizeof(Z) == sizeof(cf) && !h->prm.simt_gemm) {
+        // complex64 with tensor-core products: a dense block factors at tensor-core rate while
+        // the formatted arithmetic below it runs small, latency-bound kernels, so merge from
+        // the coarsest level whose dense storage fits in 40 % of the free device memory
+        size_t fr = 0, tot = 0;
+        HM_CUDA(cudaMemGetInfo(&fr, &tot));
+        const int L = dense_level_by_memory<Z>(h, root, 0.4 * (double)fr / sizeof(Z));
+        if (L >= 0) return L;
+    }
     const int cap = sizeof(Z) == sizeof(cf) ? 4096 : 1280;
     const int L = dense_level_by_storage<Z>(h, root, cap, 0.35);
     return L >= 0 ? L : level_of(640);
@@ -272,8 +284,6 @@ hm_status hm_build_geometry(hm_handle h, const hm_body *bodies, int nbodies, int
             if (nodes_per_dir > 12) throw HmError{HM_ERR_ARG, "N-Mueller: nodes_per_dir at most 12"};
             if (!(p->k0 > 0.0)) throw HmError{HM_ERR_ARG, "N-Mueller: k0 must be positive"};
         }
-        if (p->factor_leaf > (p->precision == HM_FP32_REFINED ? 4096 : 1280))
-            throw HmError{HM_ERR_ARG, "factor_leaf above 4096 (complex64 factor) or 1280 (complex128)"};
         if (!(p->trunc_tol >= 0.0) || p->quad_order < 0 || (p->quad_order > 0 && (p->quad_order < 4 || p->quad_order > 36)))
             throw HmError{HM_ERR_ARG, "trunc_tol must be >= 0 and quad_order 0 or 4..36"};
         if (p->precision != HM_FP64 && p->precision != HM_FP32_REFINED) throw HmError{HM_ERR_ARG, "unsupported precision"};
@@ -615,6 +625,9 @@ hm_status hm_factor(hm_handle h)
         h->trunc_log.clear();
         gemm_timing_collect(h);
         h->kgemm_s = h->kgemm_flops = h->kgemm_n = 0;
+        h->ktc_s = h->ktc_flops = h->ktc_n = 0;
+        phase_collect(h);
+        h->phase_s[PH_LU_PANEL] = h->phase_s[PH_LU_U12] = h->phase_s[PH_TILE_BUILD] = 0;
         if (h->prm.precision == HM_FP32_REFINED) {
             // the FP64 H-matrix stays unfactored: it is the refinement operator
             Timer t(h->stream);
@@ -623,7 +636,15 @@ hm_status hm_factor(hm_handle h)
             free_tree(h, h->blocks32);
             h->dirty32.clear();
             h->root32 = clone_tree<cf>(h, h->root, h->blocks32);
-            // the factor only needs factor_tol: recompress the copied low-rank leaves first
+            // with tensor-core products the dense level does not depend on the ranks: merge
+            // first, so that only the low-rank leaves that stay are recompressed
+            const bool merge_first = !h->prm.simt_gemm && h->prm.factor_leaf >= 0;
+            int lev = -1;
+            if (merge_first) {
+                lev = dense_level<cf>(h, h->root32);
+                if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
+            }
+            // the factor only needs factor_tol: recompress the copied low-rank leaves
             std::vector<Block32 *> lr;
             std::vector<int> ranks;
             for (Block32 *b : h->blocks32)
@@ -632,8 +653,10 @@ hm_status hm_factor(hm_handle h)
                     ranks.push_back(b->k);
                 }
             batched_truncate<cf>(h, lr, ranks, h->factor_tol);
-            const int lev = dense_level<cf>(h, h->root32);
-            if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
+            if (!merge_first) {
+                lev = dense_level<cf>(h, h->root32);
+                if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
+            }
             h->dense_lev = lev;
             if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
                 Block32 *d = first_diagonal_leaf(h->root32);
@@ -644,6 +667,7 @@ hm_status hm_factor(hm_handle h)
             h->tfac32 = tile_build<cf>(h, h->root32, true);
             if (!h->tmat64) h->tmat64 = tile_build<zc>(h, h->root, false);
             h->t_factor = t.stop();
+            tc_check(h);
             gemm_timing_collect(h);
             h->state = 3;
             return;
@@ -756,13 +780,19 @@ static bool refine_solve(hm_handle_s *h, int nrhs, const zc *b, zc *x)
     double worst = 1.0;
     for (it = 1; it <= h->prm.refine_max_iter; ++it) {
         convert_vec(h, r, r32, n);
-        tile_solve<cf>(h, h->tfac32, r32, nrhs);
+        {
+            PhaseScope ps(h, PH_SOLVE_SWEEP);
+            tile_solve<cf>(h, h->tfac32, r32, nrhs);
+        }
         convert_vec(h, r32, d, n);
         k_axpy1<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(d, x, n);
         HM_CHECK_LAUNCH();
         count_launch(h);
         HM_CUDA(cudaMemcpyAsync(r, b, sizeof(zc) * n, cudaMemcpyDeviceToDevice, h->stream));
-        tile_matvec<zc>(h, h->tmat64, x, r, nrhs, zmake(-1, 0));
+        {
+            PhaseScope ps(h, PH_SOLVE_MATVEC);
+            tile_matvec<zc>(h, h->tmat64, x, r, nrhs, zmake(-1, 0));
+        }
         std::vector<double> rn = colnorm2(h, r, nrhs, d_nrm);
         worst = 0;
         bool finite = true;
@@ -799,6 +829,8 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
             dirs[6 * r + d] = inc[3 * r + d];
             dirs[6 * r + 3 + d] = pol[3 * r + d];
         }
+    phase_collect(h);
+    h->phase_s[PH_SOLVE_SWEEP] = h->phase_s[PH_SOLVE_MATVEC] = 0;
     Timer t(h->stream);
     double *d_dirs = (double *)dalloc(h, sizeof(double) * dirs.size());
     HM_CUDA(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, h->stream));
@@ -820,7 +852,10 @@ static void solve_dev(hm_handle_s *h, int nrhs, const double *inc, const double 
         launch_permute(h, nrhs, x, x_dev, h->d_iperm);
         dfree(h, x);
     } else {
-        tile_solve<zc>(h, h->tfac64, b, nrhs);
+        {
+            PhaseScope ps(h, PH_SOLVE_SWEEP);
+            tile_solve<zc>(h, h->tfac64, b, nrhs);
+        }
         launch_permute(h, nrhs, b, x_dev, h->d_iperm);
         h->refine_iters = 0;
         h->refine_res = 0;
@@ -953,6 +988,14 @@ hm_status hm_query(hm_handle h, int what, double *out)
         case HM_Q_KGEMM_SECONDS: gemm_timing_collect(h); *out = h->kgemm_s; break;
         case HM_Q_KGEMM_FLOPS: gemm_timing_collect(h); *out = h->kgemm_flops; break;
         case HM_Q_KGEMM_LAUNCHES: gemm_timing_collect(h); *out = h->kgemm_n; break;
+        case HM_Q_KTC_SECONDS: gemm_timing_collect(h); *out = h->ktc_s; break;
+        case HM_Q_KTC_FLOPS: gemm_timing_collect(h); *out = h->ktc_flops; break;
+        case HM_Q_KTC_LAUNCHES: gemm_timing_collect(h); *out = h->ktc_n; break;
+        case HM_Q_T_LU_PANEL: phase_collect(h); *out = h->phase_s[PH_LU_PANEL]; break;
+        case HM_Q_T_LU_U12: phase_collect(h); *out = h->phase_s[PH_LU_U12]; break;
+        case HM_Q_T_TILE_BUILD: phase_collect(h); *out = h->phase_s[PH_TILE_BUILD]; break;
+        case HM_Q_T_SOLVE_SWEEP: phase_collect(h); *out = h->phase_s[PH_SOLVE_SWEEP]; break;
+        case HM_Q_T_SOLVE_MATVEC: phase_collect(h); *out = h->phase_s[PH_SOLVE_MATVEC]; break;
         case HM_Q_STORAGE32: {
             // the blocks reachable from the factor's root (a coarsened tree detaches the
             // blocks it merged)
@@ -985,6 +1028,38 @@ hm_status hm_get_trunc_log_host(hm_handle h, int *nbatches, double *out)
         if (!nbatches) throw HmError{HM_ERR_ARG, "null count"};
         *nbatches = (int)(h->trunc_log.size() / 7);
         if (out) std::copy(h->trunc_log.begin(), h->trunc_log.end(), out);
+    });
+}
+
+hm_status hm_cgemm(hm_handle h, char opA, char opB, int m, int n, int k, const float *alpha, const void *A, int lda,
+                   const void *B, int ldb, const float *beta, void *C, int ldc, int path)
+{
+    return guard(h, [&] {
+        if ((opA != 'N' && opA != 'C') || (opB != 'N' && opB != 'C') || !alpha || !beta)
+            throw HmError{HM_ERR_ARG, "hm_cgemm: op must be 'N' or 'C'; alpha, beta non-null"};
+        if (m < 0 || n < 0 || k < 0 || path < 0 || path > 2) throw HmError{HM_ERR_ARG, "hm_cgemm: bad size or path"};
+        if (m == 0 || n == 0) return;
+        const int rowsA = opA == 'N' ? m : k, rowsB = opB == 'N' ? k : n;
+        if (!C || ldc < std::max(1, m) || (k > 0 && (!A || !B || lda < std::max(1, rowsA) || ldb < std::max(1, rowsB))))
+            throw HmError{HM_ERR_ARG, "hm_cgemm: null pointer or leading dimension too small"};
+        if (path == 2 && (m < 64 || n < 64 || k < 16))
+            throw HmError{HM_ERR_ARG, "hm_cgemm: the tensor-core path needs m, n >= 64 and k >= 16"};
+        const cf al = cmk<cf>(alpha[0], alpha[1]), be = cmk<cf>(beta[0], beta[1]);
+        const int saved = h->prm.simt_gemm;
+        try {
+            if (path == 2) {
+                tc_gemm(h, opA, opB, m, n, k, al, (const cf *)A, lda, (const cf *)B, ldb, be, (cf *)C, ldc);
+            } else {
+                if (path == 1) h->prm.simt_gemm = 1;
+                zgemm<cf>(h, opA, opB, m, n, k, al, (const cf *)A, lda, (const cf *)B, ldb, be, (cf *)C, ldc);
+            }
+        } catch (...) {
+            h->prm.simt_gemm = saved;
+            throw;
+        }
+        h->prm.simt_gemm = saved;
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        tc_check(h);
     });
 }
 
@@ -1031,7 +1106,12 @@ void hm_destroy(hm_handle h)
         cudaEventDestroy(t.e0);
         cudaEventDestroy(t.e1);
     }
+    for (const PhaseMark &m : h->phase_pending) {
+        cudaEventDestroy(m.e0);
+        cudaEventDestroy(m.e1);
+    }
     for (cudaEvent_t e : h->gemm_free) cudaEventDestroy(e);
+    if (h->d_tc_err) cudaFree(h->d_tc_err);
     delete h;
 }
 

@@ -676,6 +676,19 @@ int dense_level_by_storage(hm_handle_s *h, BlockT<Z> *root, int cap, double thet
     return -1;
 }
 
+// The coarsest cluster level at which merging every non-low-rank block into one dense block
+// keeps the tree's storage within budget_words complex words (-1: none).
+template <class Z>
+int dense_level_by_memory(hm_handle_s *h, BlockT<Z> *root, double budget_words)
+{
+    std::vector<double> hw, dw;
+    level_words(h, root, hw, dw);
+    const double total = subtree_words(root);
+    for (int L = 0; L < (int)hw.size(); ++L)
+        if (dw[L] > 0 && total - hw[L] + dw[L] <= budget_words) return L;
+    return -1;
+}
+
 #define HM_INST_HLU(Z)                                                                             \
     template void hlu_factor<Z>(hm_handle_s *, BlockT<Z> *, double);                               \
     template void hsolve<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>);                                   \
@@ -683,7 +696,8 @@ int dense_level_by_storage(hm_handle_s *h, BlockT<Z> *root, int cap, double thet
     template BlockT<Z> *clone_tree<Z>(hm_handle_s *, Block *, std::vector<BlockT<Z> *> &);         \
     template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);                         \
     template void coarsen_tree<Z>(hm_handle_s *, BlockT<Z> *, int);                                \
-    template int dense_level_by_storage<Z>(hm_handle_s *, BlockT<Z> *, int, double);
+    template int dense_level_by_storage<Z>(hm_handle_s *, BlockT<Z> *, int, double);              \
+    template int dense_level_by_memory<Z>(hm_handle_s *, BlockT<Z> *, double);
 HM_INST_HLU(zc)
 HM_INST_HLU(cf)
 template void convert_vec<zc, cf>(hm_handle_s *, const zc *, cf *, size_t);

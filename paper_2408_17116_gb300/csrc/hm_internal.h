@@ -80,9 +80,18 @@ template <class C>
 struct TileOp;
 
 // A product timed with CUDA events (hm_linalg.cu), read after the next synchronisation.
+// Named phases timed with CUDA events on the handle's stream (PhaseScope), summed by
+// phase_collect at the next synchronisation point.
+enum PhaseId { PH_LU_PANEL = 0, PH_LU_U12, PH_TILE_BUILD, PH_SOLVE_SWEEP, PH_SOLVE_MATVEC, PH_COUNT };
+struct PhaseMark {
+    int id;
+    cudaEvent_t e0, e1;
+};
+
 struct GemmTiming {
     cudaEvent_t e0, e1;
     double flops;
+    int kind = 0;  // 0: CUDA-core k_zgemm (complex flops), 1: tensor-core k_tc_gemm (BF16 tensor flops)
 };
 
 struct hm_handle_s {
@@ -161,6 +170,14 @@ struct hm_handle_s {
     std::vector<GemmTiming> gemm_pending;
     std::vector<cudaEvent_t> gemm_free;
     double kgemm_s = 0, kgemm_flops = 0, kgemm_n = 0;
+    double ktc_s = 0, ktc_flops = 0, ktc_n = 0;
+    std::vector<PhaseMark> phase_pending;
+    double phase_s[PH_COUNT] = {0, 0, 0, 0, 0};
+    // tensor-core products (hm_tc.cu): packed-operand workspace (grow-only) and the
+    // device flag of an expired pipeline wait
+    void *tc_ws = nullptr;
+    size_t tc_ws_bytes = 0;
+    int *d_tc_err = nullptr;
     // block-row plans (hm_tiles.cu): product with the FP64 H-matrix, sweeps of the factors
     TileOp<zc> *tmat64 = nullptr, *tmatcopy = nullptr, *tfac64 = nullptr;
     TileOp<cf> *tfac32 = nullptr;
@@ -241,6 +258,38 @@ int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const 
 template <class C>
 void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std::vector<int> &ranks, double tol);
 
+void phase_collect(hm_handle_s *h);
+struct PhaseScope {
+    hm_handle_s *h;
+    int id;
+    cudaEvent_t e0;
+    bool open = true;
+    PhaseScope(hm_handle_s *h_, int id_) : h(h_), id(id_)
+    {
+        e0 = gemm_event(h);
+        HM_CUDA(cudaEventRecord(e0, h->stream));
+    }
+    void end()
+    {
+        if (!open) return;
+        open = false;
+        cudaEvent_t e1 = gemm_event(h);
+        if (cudaEventRecord(e1, h->stream) == cudaSuccess) {
+            h->phase_pending.push_back(PhaseMark{id, e0, e1});
+        } else {
+            h->gemm_free.push_back(e0);
+            h->gemm_free.push_back(e1);
+        }
+    }
+    ~PhaseScope() { end(); }
+};
+
+// ---- hm_tc.cu (complex64 GEMM on the tensor cores, split-BF16) ----
+bool tc_eligible(const hm_handle_s *h, int m, int n, int k);
+void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, const cf *A, int lda, const cf *B,
+             int ldb, cf beta, cf *Cm, int ldc);
+void tc_check(hm_handle_s *h);  // after a synchronisation: HM_ERR_TIMEOUT if a pipeline wait expired
+
 // ---- hm_io.cu ----
 void launch_rhs(hm_handle_s *h, int nrhs, const double *d_dirs, zc *d_b);  // tree order
 void launch_permute(hm_handle_s *h, int nrhs, const zc *src, zc *dst, const int *map);
@@ -266,6 +315,9 @@ void coarsen_tree(hm_handle_s *h, BlockT<C> *root, int level);
 // least theta of their dense size (-1: none).
 template <class C>
 int dense_level_by_storage(hm_handle_s *h, BlockT<C> *root, int cap, double theta);
+// Coarsest level whose merge keeps the tree's storage within budget_words (-1: none).
+template <class C>
+int dense_level_by_memory(hm_handle_s *h, BlockT<C> *root, double budget_words);
 // y[i] = (To) x[i] for n complex values
 template <class Ti, class To>
 void convert_vec(hm_handle_s *h, const Ti *x, To *y, size_t n);

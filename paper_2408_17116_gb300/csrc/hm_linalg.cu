@@ -177,6 +177,12 @@ void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, C alpha, con
         count_launch(h);
         return;
     }
+    if constexpr (std::is_same<C, cf>::value) {
+        if (tc_eligible(h, m, n, k)) {
+            tc_gemm(h, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc);
+            return;
+        }
+    }
     GemmArgs<C> g;
     g.opA = (opA == 'C');
     g.opB = (opB == 'C');
@@ -231,6 +237,17 @@ void zgemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, C alpha, con
     }
 }
 
+void phase_collect(hm_handle_s *h)
+{
+    for (const PhaseMark &m : h->phase_pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, m.e0, m.e1) == cudaSuccess) h->phase_s[m.id] += 1e-3 * ms;
+        h->gemm_free.push_back(m.e0);
+        h->gemm_free.push_back(m.e1);
+    }
+    h->phase_pending.clear();
+}
+
 cudaEvent_t gemm_event(hm_handle_s *h)
 {
     if (h->gemm_free.empty()) {
@@ -250,9 +267,15 @@ void gemm_timing_collect(hm_handle_s *h)
     for (const GemmTiming &t : h->gemm_pending) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
-            h->kgemm_s += 1e-3 * ms;
-            h->kgemm_flops += t.flops;
-            h->kgemm_n += 1;
+            if (t.kind) {
+                h->ktc_s += 1e-3 * ms;
+                h->ktc_flops += t.flops;
+                h->ktc_n += 1;
+            } else {
+                h->kgemm_s += 1e-3 * ms;
+                h->kgemm_flops += t.flops;
+                h->kgemm_n += 1;
+            }
         }
         h->gemm_free.push_back(t.e0);
         h->gemm_free.push_back(t.e1);
@@ -440,7 +463,20 @@ __global__ void k_laswp_range(C *A, int lda, int c_lo, int c_hi, int n, const in
     }
 }
 
-#define LU_NB 32
+template <class C>
+__global__ void k_eye(C *I, int n)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < (size_t)n * n) I[idx] = cmk<C>((idx % n) == (idx / n) ? 1 : 0, 0);
+}
+
+template <class C>
+static void trsm_left(hm_handle_s *h, int mode, const C *T, int ldt, int n, MVT<C> X);
+template <class C>
+void zcopy2d(hm_handle_s *h, MVT<C> dst, MVT<C> src);
+
+#define LU_NB 32    // columns of a panel step (one CTA)
+#define LU_NBO 256  // columns of an outer step: its trailing update is a product of depth 256
 
 template <class C>
 void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
@@ -454,25 +490,68 @@ void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
         count_launch(h);
         return;
     }
-    // blocked right-looking LU (the same partial pivoting over the whole block): panel,
-    // interchanges on the other columns, U12 = L11^-1 A12, A22 -= L21 U12
+    // blocked right-looking LU with the same partial pivoting over the whole block, in two
+    // levels: an outer step factors a column panel of LU_NBO columns (inner steps of LU_NB
+    // columns whose updates stay inside the panel), applies its interchanges to the other
+    // columns, forms U12 = L11^-1 A12 and updates A22 -= L21 U12 with one product of depth
+    // LU_NBO (the tensor cores for complex64)
     const double saved = h->flops_factor;
-    for (int j0 = 0; j0 < n; j0 += LU_NB) {
-        const int nb = std::min(LU_NB, n - j0), rest = n - j0 - nb;
-        k_getf2_panel<C><<<1, 512, 0, h->stream>>>(n, A, lda, j0, nb, piv, d_info);
-        HM_CHECK_LAUNCH();
-        const int ncols = j0 + rest;
-        if (ncols > 0) {
-            k_laswp_range<C><<<(ncols + 127) / 128, 128, 0, h->stream>>>(A, lda, j0, j0 + nb, n, piv, j0, j0 + nb);
+    // complex64 on the tensor cores: U12 = (L11^-1) A12 as a product with the explicit
+    // inverse of the unit lower panel block (one small solve on the identity) instead of a
+    // column-sequential solve over the whole row block
+    C *work = nullptr;
+    const bool inv12 = std::is_same<C, cf>::value && !h->prm.simt_gemm && n > 2 * LU_NBO;
+    if (inv12) work = (C *)dalloc(h, sizeof(C) * ((size_t)LU_NBO * LU_NBO + (size_t)LU_NBO * (n - LU_NBO)));
+    for (int J0 = 0; J0 < n; J0 += LU_NBO) {
+        const int NB = std::min(LU_NBO, n - J0), REST = n - J0 - NB;
+        PhaseScope ps_panel(h, PH_LU_PANEL);
+        for (int j0 = J0; j0 < J0 + NB; j0 += LU_NB) {
+            const int nb = std::min(LU_NB, J0 + NB - j0), rest = J0 + NB - j0 - nb;
+            k_getf2_panel<C><<<1, 512, 0, h->stream>>>(n, A, lda, j0, nb, piv, d_info);
             HM_CHECK_LAUNCH();
+            const int ncols = NB - nb;  // the panel's other columns
+            if (ncols > 0) {
+                k_laswp_range<C><<<(ncols + 127) / 128, 128, 0, h->stream>>>(A + (size_t)J0 * lda, lda, j0 - J0,
+                                                                            j0 + nb - J0, NB, piv, j0, j0 + nb);
+                HM_CHECK_LAUNCH();
+            }
+            count_launch(h, ncols > 0 ? 2 : 1);
+            if (rest > 0) {
+                ztrsm_lln<C>(h, A + (size_t)j0 * lda + j0, lda, nb,
+                             MVT<C>{A + (size_t)(j0 + nb) * lda + j0, nb, rest, lda});
+                zgemm<C>(h, 'N', 'N', n - j0 - nb, rest, nb, cmk<C>(-1, 0), A + (size_t)j0 * lda + j0 + nb, lda,
+                         A + (size_t)(j0 + nb) * lda + j0, lda, cmk<C>(1, 0),
+                         A + (size_t)(j0 + nb) * lda + j0 + nb, lda);
+            }
         }
-        count_launch(h, ncols > 0 ? 2 : 1);
-        if (rest > 0) {
-            ztrsm_lln<C>(h, A + (size_t)j0 * lda + j0, lda, nb, MVT<C>{A + (size_t)(j0 + nb) * lda + j0, nb, rest, lda});
-            zgemm<C>(h, 'N', 'N', rest, rest, nb, cmk<C>(-1, 0), A + (size_t)j0 * lda + j0 + nb, lda,
-                     A + (size_t)(j0 + nb) * lda + j0, lda, cmk<C>(1, 0), A + (size_t)(j0 + nb) * lda + j0 + nb, lda);
+        ps_panel.end();
+        PhaseScope ps_u12(h, PH_LU_U12);
+        const int ocols = n - NB;  // columns outside the panel
+        if (ocols > 0) {
+            k_laswp_range<C><<<(ocols + 127) / 128, 128, 0, h->stream>>>(A, lda, J0, J0 + NB, n, piv, J0, J0 + NB);
+            HM_CHECK_LAUNCH();
+            count_launch(h);
+        }
+        if (REST > 0) {
+            C *A12 = A + (size_t)(J0 + NB) * lda + J0;
+            if (inv12) {
+                C *Li = work, *T12 = work + (size_t)LU_NBO * LU_NBO;
+                const size_t nn = (size_t)NB * NB;
+                k_eye<C><<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Li, NB);
+                HM_CHECK_LAUNCH();
+                count_launch(h);
+                trsm_left(h, 0, A + (size_t)J0 * lda + J0, lda, NB, MVT<C>{Li, NB, NB, NB});
+                zgemm<C>(h, 'N', 'N', NB, REST, NB, cmk<C>(1, 0), Li, NB, A12, lda, cmk<C>(0, 0), T12, NB);
+                zcopy2d<C>(h, MVT<C>{A12, NB, REST, lda}, MVT<C>{T12, NB, REST, NB});
+            } else {
+                ztrsm_lln<C>(h, A + (size_t)J0 * lda + J0, lda, NB, MVT<C>{A12, NB, REST, lda});
+            }
+            ps_u12.end();
+            zgemm<C>(h, 'N', 'N', REST, REST, NB, cmk<C>(-1, 0), A + (size_t)J0 * lda + J0 + NB, lda, A12, lda,
+                     cmk<C>(1, 0), A + (size_t)(J0 + NB) * lda + J0 + NB, lda);
         }
     }
+    if (work) dfree(h, work);
     h->flops_factor = saved;  // counted once above
 }
 
@@ -511,12 +590,12 @@ void zlaswp(hm_handle_s *h, MVT<C> X, const int *piv, int n)
 // mode 0: X = L^-1 X (unit lower); 1: X = U^-1 X (upper); 2: X = U^-H X (U^H lower, non-unit)
 template <class C>
 __global__ void __launch_bounds__(TRS_T) k_trsm_left(int mode, const C *__restrict__ T, int ldt, int n, C *X, int ldx,
-                                                      int cols)
+                                                      int cols, int cb)
 {
     extern __shared__ __align__(16) unsigned char trs_raw[];
-    C *xs = (C *)trs_raw;  // [TRS_CB][n]
-    const int c0 = blockIdx.x * TRS_CB;
-    const int nc = min(TRS_CB, cols - c0);
+    C *xs = (C *)trs_raw;  // [cb][n]
+    const int c0 = blockIdx.x * cb;
+    const int nc = min(cb, cols - c0);
     const int tid = threadIdx.x;
     for (int e = tid; e < nc * n; e += TRS_T) {
         int c = e / n, i = e - c * n;
@@ -563,29 +642,68 @@ template <class C>
 static void trsm_left(hm_handle_s *h, int mode, const C *T, int ldt, int n, MVT<C> X)
 {
     if (X.cols <= 0 || n <= 0) return;
-    size_t smem = sizeof(C) * TRS_CB * n;
+    // columns per CTA: TRS_CB, fewer when the staged columns would exceed 200 KB of shared memory
+    const int cb = (int)std::max<size_t>(1, std::min<size_t>(TRS_CB, (size_t)200 * 1024 / (sizeof(C) * (size_t)n)));
+    const size_t smem = sizeof(C) * cb * (size_t)n;
+    if (smem > 227 * 1024) throw HmError{HM_ERR_ARG, "triangular solve: block of " + std::to_string(n) + " rows too large"};
     if (smem > 48 * 1024)
         HM_CUDA(cudaFuncSetAttribute(k_trsm_left<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_trsm_left<C><<<(X.cols + TRS_CB - 1) / TRS_CB, TRS_T, smem, h->stream>>>(mode, T, ldt, n, X.p, X.ld, X.cols);
+    k_trsm_left<C><<<(X.cols + cb - 1) / cb, TRS_T, smem, h->stream>>>(mode, T, ldt, n, X.p, X.ld, X.cols, cb);
     HM_CHECK_LAUNCH();
     count_launch(h);
     h->flops_factor += 4.0 * n * (double)n * X.cols;
 }
 
+// Blocks of more than 2 TRS_BLK rows are solved in diagonal blocks of TRS_BLK rows, the rows
+// below (forward) or above (backward) updated by one product per block (the tensor cores
+// for complex64).
+#define TRS_BLK 256
+
 template <class C>
 void ztrsm_lln(hm_handle_s *h, const C *L, int ldl, int n, MVT<C> X)
 {
-    trsm_left(h, 0, L, ldl, n, X);
+    if (n <= 2 * TRS_BLK) {
+        trsm_left(h, 0, L, ldl, n, X);
+        return;
+    }
+    for (int b0 = 0; b0 < n; b0 += TRS_BLK) {
+        const int nb = std::min(TRS_BLK, n - b0), rest = n - b0 - nb;
+        trsm_left(h, 0, L + b0 + (size_t)b0 * ldl, ldl, nb, MVT<C>{X.p + b0, nb, X.cols, X.ld});
+        if (rest > 0)
+            zgemm<C>(h, 'N', 'N', rest, X.cols, nb, cmk<C>(-1, 0), L + (b0 + nb) + (size_t)b0 * ldl, ldl, X.p + b0,
+                     X.ld, cmk<C>(1, 0), X.p + b0 + nb, X.ld);
+    }
 }
 template <class C>
 void ztrsm_lun(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X)
 {
-    trsm_left(h, 1, U, ldu, n, X);
+    if (n <= 2 * TRS_BLK) {
+        trsm_left(h, 1, U, ldu, n, X);
+        return;
+    }
+    for (int b1 = n; b1 > 0; b1 -= TRS_BLK) {
+        const int b0 = std::max(0, b1 - TRS_BLK), nb = b1 - b0;
+        trsm_left(h, 1, U + b0 + (size_t)b0 * ldu, ldu, nb, MVT<C>{X.p + b0, nb, X.cols, X.ld});
+        if (b0 > 0)
+            zgemm<C>(h, 'N', 'N', b0, X.cols, nb, cmk<C>(-1, 0), U + (size_t)b0 * ldu, ldu, X.p + b0, X.ld,
+                     cmk<C>(1, 0), X.p, X.ld);
+    }
 }
 template <class C>
 void ztrsm_luh(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X)
 {
-    trsm_left(h, 2, U, ldu, n, X);
+    if (n <= 2 * TRS_BLK) {
+        trsm_left(h, 2, U, ldu, n, X);
+        return;
+    }
+    // U^H is lower triangular: forward over blocks; (U^H)[rest, b] = (U[b, rest])^H
+    for (int b0 = 0; b0 < n; b0 += TRS_BLK) {
+        const int nb = std::min(TRS_BLK, n - b0), rest = n - b0 - nb;
+        trsm_left(h, 2, U + b0 + (size_t)b0 * ldu, ldu, nb, MVT<C>{X.p + b0, nb, X.cols, X.ld});
+        if (rest > 0)
+            zgemm<C>(h, 'C', 'N', rest, X.cols, nb, cmk<C>(-1, 0), U + b0 + (size_t)(b0 + nb) * ldu, ldu, X.p + b0,
+                     X.ld, cmk<C>(1, 0), X.p + b0 + nb, X.ld);
+    }
 }
 
 // X = X U^-1 (X rows x n): one thread per row, sequential over columns.

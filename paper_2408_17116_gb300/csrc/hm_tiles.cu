@@ -21,6 +21,13 @@
 // product with the inverse over CTAs of 256 rows (three launches per step).
 // The product is one launch over every chunk of every tile plus one reduction launch.
 // Summation order is fixed, so results are deterministic.
+//
+// A dense diagonal block larger than a row tile (a merged block of the factor) is split
+// into a group of row tiles.  Its pivots permute rows across the whole block, so the
+// forward sweep of a group first subtracts the leaves left of the block from every tile of
+// the group, then applies the block's permutation to all of its rows, then substitutes
+// tile by tile with the block's own L_ij (j < i) as further left pieces.  The backward
+// sweep has no permutation: the block's U_ij (j > i) are right pieces like any other leaf.
 #include <algorithm>
 #include <cstring>
 
@@ -204,6 +211,31 @@ __global__ void k_tile_prep(int r0, int rows, int nslots, const C *__restrict__ 
     }
 }
 
+// X[r0 + j, c] -= sum_s part[s][c][j] (fixed order): the leaves left of a grouped block.
+template <class C>
+__global__ void k_tile_sub(int r0, int rows, int nslots, const C *__restrict__ part, int nrhs, int rmax, C *X,
+                           int ldx)
+{
+    const size_t n = (size_t)rows * nrhs;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / rows), j = (int)(e - (size_t)c * rows);
+        C s = X[(size_t)c * ldx + r0 + j];
+        for (int q = 0; q < nslots; ++q) s = zsub(s, part[((size_t)q * nrhs + c) * rmax + j]);
+        X[(size_t)c * ldx + r0 + j] = s;
+    }
+}
+
+// X[r0 + j, c] = z[c][j]
+template <class C>
+__global__ void k_tile_put(int r0, int rows, int nrhs, const C *__restrict__ z, C *X, int ldx)
+{
+    const size_t n = (size_t)rows * nrhs;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / rows), j = (int)(e - (size_t)c * rows);
+        X[(size_t)c * ldx + r0 + j] = z[(size_t)c * rows + j];
+    }
+}
+
 // Sweep step, part 2 (CTAs over blocks of TL_T rows): X[r0 + i, c] = sum_j Minv[i][j] z[j][c],
 // Minv the explicit inverse of the diagonal block's triangular factor (column-major).
 template <class C>
@@ -282,7 +314,14 @@ struct TileOp {
     int maxchunks = 0;
     C *d_inv = nullptr;                   // per tile: L^-1 then U^-1 (rows x rows each)
     std::vector<size_t> inv_off;
-    std::vector<const int *> gperm;       // per tile: row permutation of its pivots (device)
+    std::vector<const int *> gperm;       // per tile: row permutation of its pivots (device; null in a group)
+    // groups of row tiles splitting one dense diagonal block larger than a tile
+    std::vector<int> grp0, grpn;          // per tile: first tile of its group, tiles in the group
+    std::vector<const int *> ggperm;      // per tile: the group's row permutation (set on its first tile)
+    TPiece<C> *d_po = nullptr;            // per grouped tile: leaves left of the whole block
+    TChunk *d_co = nullptr;
+    std::vector<int> co0, co1;
+    int maxgrow = 0;                      // rows of the largest group
     std::vector<void *> owned;
 };
 
@@ -323,6 +362,29 @@ void make_chunks(const std::vector<TPiece<C>> &pcs, int p0, int p1, int rows, do
     if (p1 > s) out.push_back(TChunk{s, p1, rows, slot++});
 }
 
+// Dense pieces of more than TL_SPLIT entries are cut into column blocks so that a large
+// dense leaf (a merged block of the factor) is streamed by many CTAs, not one.
+#define TL_SPLIT (1 << 20)
+
+template <class C>
+void push_piece(std::vector<TPiece<C>> &v, const TPiece<C> &p, int rows)
+{
+    if (p.k != 0 || (double)rows * p.ncol <= TL_SPLIT) {
+        v.push_back(p);
+        return;
+    }
+    const int nb = (int)(((double)rows * p.ncol + TL_SPLIT - 1) / TL_SPLIT);
+    for (int q = 0; q < nb; ++q) {
+        const int j0 = (int)((long long)q * p.ncol / nb), j1 = (int)((long long)(q + 1) * p.ncol / nb);
+        if (j1 <= j0) continue;
+        TPiece<C> s = p;
+        s.A = p.A + (size_t)j0 * p.ld;
+        s.c0 = p.c0 + j0;
+        s.ncol = j1 - j0;
+        v.push_back(s);
+    }
+}
+
 template <class T>
 T *upload(hm_handle_s *h, const std::vector<T> &v, std::vector<void *> &owned)
 {
@@ -338,6 +400,7 @@ template <class C>
 TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
 {
     TileOp<C> *T = new TileOp<C>();
+    PhaseScope ps(h, PH_TILE_BUILD);
     try {
         std::vector<BlockT<C> *> leaves;
         collect(root, leaves);
@@ -345,25 +408,35 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
         for (BlockT<C> *b : leaves)
             if (b->r0 == b->c0 && b->nr == b->nc && b->type == B_DENSE) diag.push_back(b);
         std::sort(diag.begin(), diag.end(), [](BlockT<C> *a, BlockT<C> *b) { return a->r0 < b->r0; });
+        // row tiles: one per diagonal leaf, or a group of nearly equal tiles when the leaf has
+        // more rows than a tile holds
+        std::vector<BlockT<C> *> tdiag;  // per tile: its diagonal leaf
         int pos = 0;
         for (BlockT<C> *d : diag) {
             if (d->r0 != pos) throw HmError{HM_ERR_STATE, "tile plan: diagonal leaves do not partition the unknowns"};
-            if (d->nr > TileRows<C>::value)
-                throw HmError{HM_ERR_ARG, "tile plan: a diagonal block has more than " +
-                                              std::to_string(TileRows<C>::value) + " unknowns"};
-            T->r0.push_back(d->r0);
-            T->rows.push_back(d->nr);
-            T->rmax = std::max(T->rmax, d->nr);
+            const int nsub = (d->nr + TileRows<C>::value - 1) / TileRows<C>::value;
+            const int g0 = (int)T->r0.size();
+            for (int q = 0; q < nsub; ++q) {
+                const int o0 = (int)((long long)q * d->nr / nsub), o1 = (int)((long long)(q + 1) * d->nr / nsub);
+                T->r0.push_back(d->r0 + o0);
+                T->rows.push_back(o1 - o0);
+                T->rmax = std::max(T->rmax, o1 - o0);
+                T->grp0.push_back(g0);
+                T->grpn.push_back(nsub);
+                tdiag.push_back(d);
+            }
+            if (nsub > 1) T->maxgrow = std::max(T->maxgrow, d->nr);
             pos += d->nr;
         }
         T->N = pos;
-        T->ntile = (int)diag.size();
+        T->ntile = (int)T->r0.size();
         auto tile_of = [&](int r) {
             int i = (int)(std::upper_bound(T->r0.begin(), T->r0.end(), r) - T->r0.begin()) - 1;
             return i;
         };
-        // pieces per tile: all / left of the diagonal / right of the diagonal
-        std::vector<std::vector<TPiece<C>>> all(T->ntile), left(T->ntile), right(T->ntile);
+        // pieces per tile: all / left of the diagonal (outside the tile's own diagonal leaf, and
+        // inside it for a group) / right of the diagonal
+        std::vector<std::vector<TPiece<C>>> all(T->ntile), left(T->ntile), lin(T->ntile), right(T->ntile);
         for (BlockT<C> *b : leaves) {
             if (b->type == B_LR && b->k == 0) continue;
             const bool isdiag = b->r0 == b->c0 && b->type == B_DENSE && b->nr == b->nc;
@@ -384,12 +457,26 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                     p.V = b->V;
                     p.k = b->k;
                 }
-                all[i].push_back(p);
-                if (isdiag) continue;
+                push_piece(all[i], p, T->rows[i]);
+                if (isdiag) {
+                    // a grouped diagonal leaf: its off-diagonal tile blocks L_ij (j < i), U_ij (j > i)
+                    for (int j = T->grp0[i]; j < T->grp0[i] + T->grpn[i]; ++j) {
+                        if (j == i) continue;
+                        TPiece<C> q;
+                        q.A = b->D + rofs + (size_t)(T->r0[j] - b->r0) * b->nr;
+                        q.V = nullptr;
+                        q.ld = b->nr;
+                        q.c0 = T->r0[j];
+                        q.ncol = T->rows[j];
+                        q.k = 0;
+                        push_piece(j < i ? lin[i] : right[i], q, T->rows[i]);
+                    }
+                    continue;
+                }
                 if (b->c0 + b->nc <= T->r0[i])
-                    left[i].push_back(p);
+                    push_piece(left[i], p, T->rows[i]);
                 else if (b->c0 >= T->r0[i] + T->rows[i])
-                    right[i].push_back(p);
+                    push_piece(right[i], p, T->rows[i]);
                 else
                     throw HmError{HM_ERR_STATE, "tile plan: an off-diagonal leaf crosses the diagonal"};
             }
@@ -421,20 +508,25 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
         }
         if (factored) {
             T->factored = true;
-            std::vector<TPiece<C>> pl, pu;
-            std::vector<TChunk> cl, cu;
+            std::vector<TPiece<C>> pl, pu, po;
+            std::vector<TChunk> cl, cu, co;
             T->cl0.resize(T->ntile);
             T->cl1.resize(T->ntile);
             T->cu0.resize(T->ntile);
             T->cu1.resize(T->ntile);
+            T->co0.resize(T->ntile);
+            T->co1.resize(T->ntile);
             for (int i = 0; i < T->ntile; ++i) {
-                // about 2 CTAs per SM per step
-                double tl = 0, tu = 0;
-                for (auto &p : left[i]) tl += piece_cost(p, T->rows[i]);
+                // about 2 CTAs per SM per step; a grouped tile substitutes with its block's L_ij
+                // and subtracts the outside leaves in a separate pass
+                const bool grouped = T->grpn[i] > 1;
+                const std::vector<TPiece<C>> &L = grouped ? lin[i] : left[i];
+                double tl = 0, tu = 0, to = 0;
+                for (auto &p : L) tl += piece_cost(p, T->rows[i]);
                 for (auto &p : right[i]) tu += piece_cost(p, T->rows[i]);
-                int sl = 0, su = 0;
+                int sl = 0, su = 0, so = 0;
                 int p0 = (int)pl.size();
-                pl.insert(pl.end(), left[i].begin(), left[i].end());
+                pl.insert(pl.end(), L.begin(), L.end());
                 T->cl0[i] = (int)cl.size();
                 make_chunks(pl, p0, (int)pl.size(), T->rows[i], std::max(tl / 304.0, 1.0), cl, sl);
                 T->cl1[i] = (int)cl.size();
@@ -443,13 +535,24 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                 T->cu0[i] = (int)cu.size();
                 make_chunks(pu, p0, (int)pu.size(), T->rows[i], std::max(tu / 304.0, 1.0), cu, su);
                 T->cu1[i] = (int)cu.size();
-                T->maxchunks = std::max(T->maxchunks, std::max(sl, su));
+                T->co0[i] = T->co1[i] = (int)co.size();
+                if (grouped) {
+                    for (auto &p : left[i]) to += piece_cost(p, T->rows[i]);
+                    p0 = (int)po.size();
+                    po.insert(po.end(), left[i].begin(), left[i].end());
+                    make_chunks(po, p0, (int)po.size(), T->rows[i], std::max(to / 304.0, 1.0), co, so);
+                    T->co1[i] = (int)co.size();
+                }
+                T->maxchunks = std::max(T->maxchunks, std::max(sl, std::max(su, so)));
             }
             T->d_pl = upload(h, pl, T->owned);
             T->d_pu = upload(h, pu, T->owned);
             T->d_cl = upload(h, cl, T->owned);
             T->d_cu = upload(h, cu, T->owned);
-            // explicit inverses of the diagonal factors: L^-1 (unit lower) and U^-1
+            T->d_po = upload(h, po, T->owned);
+            T->d_co = upload(h, co, T->owned);
+            // explicit inverses of the diagonal factors of every tile: L_ii^-1 (unit lower) and
+            // U_ii^-1, from the tile's diagonal sub-block of its leaf
             size_t tot = 0;
             for (int i = 0; i < T->ntile; ++i) {
                 T->inv_off.push_back(tot);
@@ -459,20 +562,23 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
             T->owned.push_back(T->d_inv);
             for (int i = 0; i < T->ntile; ++i) {
                 const int n = T->rows[i];
+                BlockT<C> *d = tdiag[i];
+                const size_t o = (size_t)(T->r0[i] - d->r0);
+                const C *Dii = d->D + o + o * d->nr;
                 C *Li = T->d_inv + T->inv_off[i], *Ui = Li + (size_t)n * n;
                 identity_fill(h, Li, n);
                 identity_fill(h, Ui, n);
-                ztrsm_lln(h, diag[i]->D, n, n, MVT<C>{Li, n, n, n});
-                ztrsm_lun(h, diag[i]->D, n, n, MVT<C>{Ui, n, n, n});
+                ztrsm_lln(h, Dii, d->nr, n, MVT<C>{Li, n, n, n});
+                ztrsm_lun(h, Dii, d->nr, n, MVT<C>{Ui, n, n, n});
             }
-            // the pivots of each diagonal block as one gather: applying the interchanges
+            // the pivots of each diagonal leaf as one gather: applying the interchanges
             // k <-> piv[k] in order to z is z_new[j] = z_old[g[j]]
             std::vector<int> gall;
             std::vector<size_t> goff;
-            for (int i = 0; i < T->ntile; ++i) {
-                const int n = T->rows[i];
+            for (BlockT<C> *d : diag) {
+                const int n = d->nr;
                 std::vector<int> pv(n), g(n);
-                HM_CUDA(cudaMemcpyAsync(pv.data(), diag[i]->piv, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
+                HM_CUDA(cudaMemcpyAsync(pv.data(), d->piv, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
                 HM_CUDA(cudaStreamSynchronize(h->stream));
                 for (int k = 0; k < n; ++k) g[k] = k;
                 for (int k = 0; k < n; ++k) {
@@ -484,7 +590,15 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                 gall.insert(gall.end(), g.begin(), g.end());
             }
             const int *d_g = upload(h, gall, T->owned);
-            for (int i = 0; i < T->ntile; ++i) T->gperm.push_back(d_g + goff[i]);
+            T->gperm.assign(T->ntile, nullptr);
+            T->ggperm.assign(T->ntile, nullptr);
+            for (int i = 0, di = -1; i < T->ntile; ++i) {
+                if (T->grp0[i] == i) ++di;
+                if (T->grpn[i] == 1)
+                    T->gperm[i] = d_g + goff[di];
+                else if (T->grp0[i] == i)
+                    T->ggperm[i] = d_g + goff[di];
+            }
         }
     } catch (...) {
         tile_free(h, T);
@@ -526,23 +640,52 @@ void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
     if (!T->factored) throw HmError{HM_ERR_STATE, "tile_solve on an unfactored plan"};
     if (nrhs <= 0 || T->ntile == 0) return;
     C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->maxchunks, 1) * nrhs * T->rmax);
-    C *z = (C *)dalloc(h, sizeof(C) * (size_t)T->rmax * nrhs);
+    C *z = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->rmax, T->maxgrow) * nrhs);
     const size_t psmem = partial_smem<C>(T->rmax);
+    auto grid_of = [&](int rows) { return std::max(1, std::min(64, (int)((rows * (size_t)nrhs + TL_T - 1) / TL_T))); };
+    auto partial = [&](const TPiece<C> *pcs, const TChunk *chs, int nch) {
+        if (!nch) return;
+        k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(pcs, chs, X, T->N, nrhs, part, T->rmax);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+    };
     auto step = [&](int i, const TPiece<C> *pcs, const TChunk *chs, int nch, const int *g, const C *Minv) {
-        if (nch) {
-            k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(pcs, chs, X, T->N, nrhs, part, T->rmax);
-            HM_CHECK_LAUNCH();
-        }
+        partial(pcs, chs, nch);
         const int rows = T->rows[i];
-        const int gp = std::min(64, (int)((rows * (size_t)nrhs + TL_T - 1) / TL_T));
-        k_tile_prep<C><<<std::max(gp, 1), TL_T, 0, h->stream>>>(T->r0[i], rows, nch, part, nrhs, T->rmax, g, X, T->N, z);
+        k_tile_prep<C><<<grid_of(rows), TL_T, 0, h->stream>>>(T->r0[i], rows, nch, part, nrhs, T->rmax, g, X, T->N, z);
         HM_CHECK_LAUNCH();
         k_tile_mul<C><<<(rows + TL_T - 1) / TL_T, TL_T, 0, h->stream>>>(T->r0[i], rows, nrhs, Minv, z, X, T->N);
         HM_CHECK_LAUNCH();
-        count_launch(h, nch ? 3 : 2);
+        count_launch(h, 2);
     };
-    for (int i = 0; i < T->ntile; ++i)
-        step(i, T->d_pl, T->d_cl + T->cl0[i], T->cl1[i] - T->cl0[i], T->gperm[i], T->d_inv + T->inv_off[i]);
+    for (int i = 0; i < T->ntile;) {
+        const int gn = T->grpn[i];
+        if (gn == 1) {
+            step(i, T->d_pl, T->d_cl + T->cl0[i], T->cl1[i] - T->cl0[i], T->gperm[i], T->d_inv + T->inv_off[i]);
+            ++i;
+            continue;
+        }
+        // a group: the leaves left of the block, then the block's permutation, then its L
+        for (int j = i; j < i + gn; ++j) {
+            const int nch = T->co1[j] - T->co0[j];
+            if (!nch) continue;
+            partial(T->d_po, T->d_co + T->co0[j], nch);
+            k_tile_sub<C><<<grid_of(T->rows[j]), TL_T, 0, h->stream>>>(T->r0[j], T->rows[j], nch, part, nrhs,
+                                                                      T->rmax, X, T->N);
+            HM_CHECK_LAUNCH();
+            count_launch(h);
+        }
+        const int r0 = T->r0[i], rows = T->r0[i + gn - 1] + T->rows[i + gn - 1] - r0;
+        k_tile_prep<C><<<grid_of(rows), TL_T, 0, h->stream>>>(r0, rows, 0, part, nrhs, T->rmax, T->ggperm[i], X, T->N,
+                                                              z);
+        HM_CHECK_LAUNCH();
+        k_tile_put<C><<<grid_of(rows), TL_T, 0, h->stream>>>(r0, rows, nrhs, z, X, T->N);
+        HM_CHECK_LAUNCH();
+        count_launch(h, 2);
+        for (int j = i; j < i + gn; ++j)
+            step(j, T->d_pl, T->d_cl + T->cl0[j], T->cl1[j] - T->cl0[j], nullptr, T->d_inv + T->inv_off[j]);
+        i += gn;
+    }
     for (int i = T->ntile - 1; i >= 0; --i)
         step(i, T->d_pu, T->d_cu + T->cu0[i], T->cu1[i] - T->cu0[i], nullptr,
              T->d_inv + T->inv_off[i] + (size_t)T->rows[i] * T->rows[i]);

@@ -22,7 +22,8 @@ Q = dict(N=0, NNODE=1, NPATCH=2, NEAR_PAIRS=3, DENSE_BLOCKS=4, LR_BLOCKS=5, CR=6
          RANK_PRED_ERR=27, TRUNC_BATCHES=28, TRUNC_JOBS=29, TRUNC_MAXK=30, TRUNC_WORK=31, T_TRUNC=32,
          ACA_SKIPPED=33, KQR_SECONDS=34, KQR_FLOPS=35, KQR_LAUNCHES=36, KCORE_SECONDS=37,
          KCORE_FLOPS=38, KCORE_LAUNCHES=39, DENSE_LEVEL=40, KGEMM_SECONDS=41, KGEMM_FLOPS=42,
-         KGEMM_LAUNCHES=43)
+         KGEMM_LAUNCHES=43, KTC_SECONDS=44, KTC_FLOPS=45, KTC_LAUNCHES=46,
+         T_LU_PANEL=47, T_LU_U12=48, T_TILE_BUILD=49, T_SOLVE_SWEEP=50, T_SOLVE_MATVEC=51)
 RANK_NFEAT = 8
 HM_FP64, HM_FP32_REFINED = 0, 1
 HM_PEC_MFIE, HM_PEC_CFIE, HM_DIEL_MULLER = 0, 1, 2
@@ -35,7 +36,7 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
            "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host",
-           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host")
+           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host", "hm_cgemm")
 
 
 class hm_params(ctypes.Structure):
@@ -45,7 +46,7 @@ class hm_params(ctypes.Structure):
                 ("factor_tol", ctypes.c_double), ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int),
                 ("cfie_alpha", ctypes.c_double), ("eps_r_re", ctypes.c_double), ("eps_r_im", ctypes.c_double),
                 ("mu_r", ctypes.c_double), ("trunc_tol", ctypes.c_double), ("quad_order", ctypes.c_int),
-                ("factor_leaf", ctypes.c_int)]
+                ("factor_leaf", ctypes.c_int), ("simt_gemm", ctypes.c_int)]
 
 
 class hm_body(ctypes.Structure):
@@ -89,6 +90,7 @@ def load(path=SO):
     L.hm_muller_rhs_farfield_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, P, P, P, P, I, P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_inject_fault.argtypes = [P, I]
+    L.hm_cgemm.argtypes = [P, ctypes.c_char, ctypes.c_char, I, I, I, P, P, I, P, I, P, P, I, I]
     L.hm_get_trunc_log_host.argtypes = [P, ctypes.POINTER(I), P]
     L.hm_destroy.argtypes = [P]
     L.hm_destroy.restype = None
@@ -238,7 +240,7 @@ class Solver:
     def hm_build_geometry(self, bodies, ms, nc, k0, leaf, eta, aca_tol, near_delta=0.5, aca_max_rank=0,
                           keep_matrix=False, precision=HM_FP64, factor_tol=0.0, refine_tol=0.0, refine_max_iter=0,
                           formulation=HM_PEC_MFIE, cfie_alpha=0.0, eps_r=1.0, mu_r=0.0, trunc_tol=0.0,
-                          quad_order=0, factor_leaf=0):
+                          quad_order=0, factor_leaf=0, simt_gemm=False):
         self._bodies = make_bodies(bodies, ms)
         eps = complex(eps_r)
         p = hm_params(k0=float(k0), formulation=int(formulation), leaf=int(leaf), eta=float(eta),
@@ -246,7 +248,8 @@ class Solver:
                       precision=int(precision), keep_matrix=int(bool(keep_matrix)), factor_tol=float(factor_tol),
                       refine_tol=float(refine_tol), refine_max_iter=int(refine_max_iter),
                       cfie_alpha=float(cfie_alpha), eps_r_re=eps.real, eps_r_im=eps.imag, mu_r=float(mu_r),
-                      trunc_tol=float(trunc_tol), quad_order=int(quad_order), factor_leaf=int(factor_leaf))
+                      trunc_tol=float(trunc_tol), quad_order=int(quad_order), factor_leaf=int(factor_leaf),
+                      simt_gemm=int(bool(simt_gemm)))
         self._check(self.L.hm_build_geometry(self.h, self._bodies, len(ms), int(nc), ctypes.byref(p)))
         self.N = int(self.hm_query("N"))
         self.dof = 4 if int(formulation) == HM_DIEL_MULLER else 2
@@ -310,6 +313,25 @@ class Solver:
         out = np.empty((n.value, 7))
         self._check(self.L.hm_get_trunc_log_host(self.h, ctypes.byref(n), _np_ptr(out)))
         return out
+
+    def hm_cgemm(self, opA, opB, alpha, A, B, beta, C, path=0):
+        """C = alpha op(A) op(B) + beta C on complex64 CUDA tensors in column-major storage:
+        pass the transposes of row-major torch tensors (A.T etc.), i.e. A, B, C are
+        torch tensors whose .T is contiguous.  Returns C."""
+        def colmajor(X):
+            assert X.dtype == self.torch.complex64 and X.is_cuda and X.dim() == 2
+            assert X.stride(0) == 1, "column-major (X.T contiguous) expected"
+            return X.stride(1)
+        lda, ldb, ldc = colmajor(A), colmajor(B), colmajor(C)
+        m, n = C.shape
+        k = A.shape[1] if opA == "N" else A.shape[0]
+        al = (ctypes.c_float * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (ctypes.c_float * 2)(complex(beta).real, complex(beta).imag)
+        self._check(self.L.hm_cgemm(self.h, opA.encode(), opB.encode(), m, n, k, ctypes.cast(al, ctypes.c_void_p),
+                                    ctypes.c_void_p(A.data_ptr()), max(lda, 1), ctypes.c_void_p(B.data_ptr()),
+                                    max(ldb, 1), ctypes.cast(be, ctypes.c_void_p), ctypes.c_void_p(C.data_ptr()),
+                                    max(ldc, 1), int(path)))
+        return C
 
     def hm_inject_fault(self, what):
         self._check(self.L.hm_inject_fault(self.h, FAULT[what] if isinstance(what, str) else int(what)))

@@ -182,14 +182,24 @@ def test_matvec_against_dense_oracle():
     assert np.linalg.norm(y2 - ref) / np.linalg.norm(ref) < 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32r", "fp32r-fine"])
+MID = {  # precision, factor_leaf, simt_gemm
+    "fp64": (hm.HM_FP64, 0, False),            # H-LU, dense blocks from 600-unknown clusters down
+    "fp64-dense": (hm.HM_FP64, 4800, False),   # one dense block, split into a group of 3 row tiles
+    "fp32r": (hm.HM_FP32_REFINED, 0, False),   # adaptive: one dense block, tensor-core LU, 2 row tiles
+    "fp32r-h": (hm.HM_FP32_REFINED, 640, False),  # H-LU above 600-unknown dense blocks, tensor-core products
+    "fp32r-simt": (hm.HM_FP32_REFINED, 0, True),  # CUDA-core products only, storage-chosen dense level
+    "fp32r-fine": (hm.HM_FP32_REFINED, -1, False),  # the fill's leaves (leaf-level formatted arithmetic)
+}
+
+
+@pytest.mark.parametrize("precision", list(MID))
 def test_mid_size_solution_against_dense_oracle(precision):
     # 4,800 unknowns (4-wavelength sphere, leaf 128): hundreds of low-rank leaves, so the
-    # H-LU's formatted products and recompressions are exercised, in both precisions (the
-    # FP32 factor with dense blocks below 640-unknown clusters, and on the fill's leaves)
+    # H-LU's formatted products and recompressions are exercised, in both precisions, and
+    # the merged dense factor in both (grouped row tiles in the substitution)
     wl, o, A, b, xo = oracle_for("sphere_d4_m2_nc10")
-    prec = hm.HM_FP64 if precision == "fp64" else hm.HM_FP32_REFINED
-    s = make_solver(wl, precision=prec, factor_leaf=-1 if precision == "fp32r-fine" else 0)
+    prec, fleaf, simt = MID[precision]
+    s = make_solver(wl, precision=prec, factor_leaf=fleaf, simt_gemm=simt)
     s.hm_fill()
     assert s.hm_query("LR_BLOCKS") >= MIN_LOWRANK["sphere_d4_m2_nc10"]
     s.hm_factor()
@@ -234,7 +244,7 @@ def test_error_codes_and_call_order():
 @pytest.mark.parametrize("name", SMALL)
 def test_fp32_factor_with_fp64_refinement_against_dense_oracle(name, factor_leaf):
     # FP32 H-LU as a preconditioner, FP64 refinement against the FP64 H-matrix; factor_leaf 0:
-    # the factor's blocks below 640-unknown clusters merged into dense blocks, -1: the fill's
+    # adaptive (at these sizes the whole matrix fits as one dense block), -1: the fill's
     # block structure (leaf-level formatted arithmetic in FP32)
     wl, o, A, b, xo = oracle_for(name)
     s = make_solver(wl, precision=hm.HM_FP32_REFINED, factor_leaf=factor_leaf)
