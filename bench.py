@@ -281,7 +281,7 @@ def one_step(s, wl, dirs, host=False, precision="fp32r"):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="sphere_d8_m4_nc10")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -293,8 +293,9 @@ def main():
                     help="skip the host-buffer end-to-end step (for kernel launch lists under a profiler)")
     ap.add_argument("--full-oracle", action="store_true",
                     help="with --impl reference: time the oracle's full dense fill, LU and solve once")
-    ap.add_argument("--compare-workload", default="sphere_d2_m2_nc6",
-                    help="workload of the FP32-refined vs plain-FP64 comparison (one step each)")
+    ap.add_argument("--compare-workload", default=None,
+                    help="workload of the FP32-refined vs plain-FP64 comparison, one step each "
+                         "(default: the bench workload)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -366,7 +367,8 @@ def main():
     stats = {k.lower(): s.hm_query(k) for k in ("CR", "MAX_RANK", "MEAN_RANK", "LR_BLOCKS", "DENSE_BLOCKS",
                                                  "NEAR_PAIRS", "ACA_NONCONV", "FLOPS_FACTOR", "REFINE_ITERS",
                                                  "REFINE_RES", "STORAGE", "STORAGE32", "DENSE_LEVEL",
-                                                 "TRUNC_BATCHES", "TRUNC_JOBS", "TRUNC_MAXK")}
+                                                 "TRUNC_BATCHES", "TRUNC_JOBS", "TRUNC_MAXK", "T_LU_PANEL",
+                                                 "T_LU_U12", "T_TILE_BUILD", "T_SOLVE_SWEEP", "T_SOLVE_MATVEC")}
     # e2e: host buffers in and out, wall clock around the public API calls
     e2e_s = None
     if not args.no_e2e:
@@ -440,20 +442,22 @@ def main():
            "roofline": roof, "kernels": cands[1:]}
     if not args.no_compare:
         # FP32 H-LU + FP64 refinement against the plain FP64 H-LU on the same GPU, one timed
-        # step each on a workload the FP64 path finishes in about a minute
-        cwl = load_workload(args.compare_workload)
-        cmp = {"workload": args.compare_workload}
+        # step each, with each solution's error against the stored dense-oracle solution
+        cname = args.compare_workload or args.workload
+        cwl = load_workload(cname)
+        cmp = {"workload": cname}
         for p in ("fp32r", "fp64"):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             barrier()
             e0.record(stream)
-            one_step(s, cwl, dirs, precision=p)
+            cx, _ = one_step(s, cwl, dirs, precision=p)
             e1.record(stream)
             barrier()
             cms = e0.elapsed_time(e1)
             cmp[p] = {"value": s.N / (cms / 1000.0), "unit": "unknowns/s", "ms_per_step": cms, "unknowns": s.N,
                       "phases_s": {k: s.hm_query(k) for k in phases}, "refine_iters": s.hm_query("REFINE_ITERS"),
-                      "refine_res": s.hm_query("REFINE_RES")}
+                      "refine_res": s.hm_query("REFINE_RES"), "dense_level": s.hm_query("DENSE_LEVEL"),
+                      "solution_error_vs_oracle": solution_error(cname, cx)}
         cmp["fp32r_speedup"] = cmp["fp64"]["ms_per_step"] / cmp["fp32r"]["ms_per_step"]
         out["compare"] = cmp
         progress("compare: %s" % json.dumps(cmp))

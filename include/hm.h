@@ -92,11 +92,12 @@ typedef struct {
     int factor_leaf;      /* the H-LU stores, as one dense block each (an exact merge), the hierarchical
                              blocks of one cluster level and of every level below it: > 0, the first
                              level whose clusters hold at most factor_leaf unknowns; 0 (adaptive):
-                             HM_FP32_REFINED with tensor-core products, the coarsest level whose merged
-                             storage fits in 40 % of the free device memory (the whole matrix, when it
-                             fits); otherwise the coarsest level of clusters of at most 4096 (complex64)
-                             / 1280 (complex128) unknowns whose non-low-rank blocks store at least 35 %
-                             of their dense size, else the level of 640-unknown clusters; negative, the
+                             the coarsest level whose merged storage fits in 40 % of the free device
+                             memory (the whole matrix, when it fits), for products on the CUDA cores
+                             (complex128, or simt_gemm) no coarser than clusters of 24,576 unknowns;
+                             when no level fits, the coarsest level of clusters of at most 4096
+                             (complex64) / 1280 (complex128) unknowns whose non-low-rank blocks store at
+                             least 35 % of their dense size, else the level of 640-unknown clusters; negative, the
                              fill's block structure.  HM_FP64: applies to the H-matrix factored in
                              place; HM_FP32_REFINED: to the complex64 copy (the FP64 H-matrix is kept). */
     int simt_gemm;        /* HM_FP32_REFINED: nonzero keeps every complex64 product of the H-LU on the

@@ -214,14 +214,17 @@ static int dense_level(hm_handle_s *h, BlockT<Z> *root)
         return lev;
     };
     if (h->prm.factor_leaf > 0) return level_of(h->prm.factor_leaf);
-    if (sizeof(Z) == sizeof(cf) && !h->prm.simt_gemm) {
-        // complex64 with tensor-core products: a dense block factors at tensor-core rate while
-        // the formatted arithmetic below it runs small, latency-bound kernels, so merge from
-        // the coarsest level whose dense storage fits in 40 % of the free device memory
-        size_t fr = 0, tot = 0;
-        HM_CUDA(cudaMemGetInfo(&fr, &tot));
-        const int L = dense_level_by_memory<Z>(h, root, 0.4 * (double)fr / sizeof(Z));
-        if (L >= 0) return L;
+    // A dense block factors at the rate of large products (tensor cores for complex64, the
+    // FP64 pipe at its peak for complex128) while the formatted arithmetic below it runs
+    // small, latency-bound kernels: merge from the coarsest level whose dense storage fits
+    // in 40 % of the free device memory.  Without tensor cores the dense blocks are kept to
+    // clusters of at most 24,576 unknowns (a dense FP64 LU of that size takes seconds).
+    size_t fr = 0, tot = 0;
+    HM_CUDA(cudaMemGetInfo(&fr, &tot));
+    const int Lm = dense_level_by_memory<Z>(h, root, 0.4 * (double)fr / sizeof(Z));
+    if (Lm >= 0) {
+        if (sizeof(Z) == sizeof(cf) && !h->prm.simt_gemm) return Lm;
+        return std::max(Lm, level_of(24576));
     }
     const int cap = sizeof(Z) == sizeof(cf) ? 4096 : 1280;
     const int L = dense_level_by_storage<Z>(h, root, cap, 0.35);

@@ -506,6 +506,7 @@ void hlu_factor(hm_handle_s *h, BlockT<Z> *root, double tol)
     HM_CUDA(cudaStreamSynchronize(h->stream));
     dfree(h, d_info);
     h->cur_tol = saved;
+    if (info < 0) throw HmError{HM_ERR_TIMEOUT, "H-LU: a bounded grid barrier of the panel LU expired"};
     if (info) throw HmError{HM_ERR_SINGULAR, "H-LU: zero pivot in a diagonal leaf"};
 }
 

@@ -445,6 +445,260 @@ __global__ void __launch_bounds__(512) k_getf2_panel(int m, C *A, int lda, int j
     }
 }
 
+// ---------------------------------------------------------------------------
+// Panel LU on many CTAs (tall panels): columns [j0, j0 + nb) of an n x n block over rows
+// [j0, n).  The rows are split into slabs of R rows, one slab per CTA, held in shared
+// memory for the whole panel.  Per column k each CTA proposes the entry of largest
+// modulus in its slab together with that row (and the owner of row k publishes row k);
+// after one grid barrier every CTA takes the same pivot (largest modulus, ties to the
+// lowest row), the owners of rows k and p exchange them, and each CTA scales its part of
+// the column and updates its slab.  Proposals are double-buffered by column parity (no CTA
+// runs more than one barrier ahead of another).  The same partial pivoting as the
+// one-CTA panel; the barrier waits are bounded (2 s): on expiry info is set to -1.
+// ---------------------------------------------------------------------------
+#define PC_T 256
+#define PC_NBMAX 64
+
+struct GridBar {
+    unsigned count, gen;
+};
+
+__device__ __forceinline__ uint64_t pc_timer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All CTAs of the (cooperative) grid meet; false on a 2 s timeout or when another CTA
+// has reported one (info < 0).
+__device__ bool pc_barrier(GridBar *gb, unsigned nblocks, int *info)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &gb->gen;
+        const unsigned my = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const uint64_t t0 = pc_timer();
+            for (unsigned it = 1; *vgen == my; ++it) {
+                if ((it & 1023) == 0) {
+                    if (*(volatile int *)info < 0 || pc_timer() - t0 > 2000000000ull) {
+                        atomicExch(info, -1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// (v, p) reduction over the CTA: largest v, ties to the lowest p; w travels with p.
+template <class R>
+__device__ void pc_argmax(R &v, int &p, int &w)
+{
+    __shared__ R sv[PC_T / 32];
+    __shared__ int sp[PC_T / 32], sw[PC_T / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        R v2 = __shfl_down_sync(0xffffffffu, v, o);
+        int p2 = __shfl_down_sync(0xffffffffu, p, o), w2 = __shfl_down_sync(0xffffffffu, w, o);
+        if (v2 > v || (v2 == v && p2 < p)) {
+            v = v2;
+            p = p2;
+            w = w2;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sv[warp] = v;
+        sp[warp] = p;
+        sw[warp] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < PC_T / 32; ++q)
+            if (sv[q] > v || (sv[q] == v && sp[q] < p)) {
+                v = sv[q];
+                p = sp[q];
+                w = sw[q];
+            }
+        sv[0] = v;
+        sp[0] = p;
+        sw[0] = w;
+    }
+    __syncthreads();
+    v = sv[0];
+    p = sp[0];
+    w = sw[0];
+    __syncthreads();
+}
+
+template <class C>
+__global__ void __launch_bounds__(PC_T) k_getf2_coop(int n, C *A, int lda, int j0, int nb, int R, int *piv, int *info,
+                                                     C *cand_rows, typename CReal<C>::R *cand_val, int *cand_pos,
+                                                     C *krow, GridBar *gb)
+{
+    typedef typename CReal<C>::R Rl;
+    extern __shared__ __align__(16) unsigned char pc_raw[];
+    C *S = (C *)pc_raw;  // S[j * R + i] = A[r0 + i, j0 + j]
+    __shared__ C s_prow[PC_NBMAX];
+    const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
+    const int r0 = j0 + c * R;
+    const int rn = max(0, min(R, n - r0));
+    for (int e = tid; e < nb * R; e += PC_T) {
+        const int j = e / R, i = e - j * R;
+        S[e] = i < rn ? A[(size_t)(j0 + j) * lda + r0 + i] : cmk<C>(0, 0);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < nb; ++kk) {
+        const int k = j0 + kk, par = kk & 1;
+        // 1. this slab's proposal among rows >= k
+        Rl v = -1;
+        int p = 0x7fffffff, w = c;
+        for (int i = max(0, k - r0) + tid; i < rn; i += PC_T) {
+            const Rl a = zabs2(S[kk * R + i]);
+            if (a > v || (a == v && r0 + i < p)) {
+                v = a;
+                p = r0 + i;
+            }
+        }
+        pc_argmax(v, p, w);
+        // 2. publish it (and row k from its owner)
+        if (tid == 0) {
+            cand_val[par * G + c] = v;
+            cand_pos[par * G + c] = p;
+        }
+        if (p != 0x7fffffff)
+            for (int j = tid; j < nb; j += PC_T) cand_rows[((size_t)par * G + c) * nb + j] = S[j * R + (p - r0)];
+        if (k >= r0 && k < r0 + rn)
+            for (int j = tid; j < nb; j += PC_T) krow[par * nb + j] = S[j * R + (k - r0)];
+        __threadfence();
+        // 3. all proposals are in
+        if (!pc_barrier(gb, G, info)) return;
+        // 4. the common pivot
+        v = -1;
+        p = 0x7fffffff;
+        w = 0;
+        for (int q = tid; q < G; q += PC_T) {
+            const Rl vq = __ldcg(cand_val + par * G + q);
+            const int pq = __ldcg(cand_pos + par * G + q);
+            if (pq != 0x7fffffff && (vq > v || (vq == v && pq < p))) {
+                v = vq;
+                p = pq;
+                w = q;
+            }
+        }
+        pc_argmax(v, p, w);
+        if (p < k || p >= n) p = k;  // cannot happen: the owner of row k always proposes
+        for (int j = tid; j < nb; j += PC_T) s_prow[j] = __ldcg(cand_rows + ((size_t)par * G + w) * nb + j);
+        if (c == 0 && tid == 0) {
+            piv[k] = p;
+            if (!(v > 0) && *info == 0) *info = k + 1;
+        }
+        __syncthreads();
+        // 5. rows k and p change places
+        if (p != k) {
+            if (k >= r0 && k < r0 + rn)
+                for (int j = tid; j < nb; j += PC_T) S[j * R + (k - r0)] = s_prow[j];
+            if (p >= r0 && p < r0 + rn)
+                for (int j = tid; j < nb; j += PC_T) S[j * R + (p - r0)] = __ldcg(krow + par * nb + j);
+        }
+        __syncthreads();
+        // 6. multipliers and the rank-1 update of the slab below row k
+        const C inv = v > 0 ? zdiv(cmk<C>(1, 0), s_prow[kk]) : cmk<C>(0, 0);
+        for (int i = max(0, k + 1 - r0) + tid; i < rn; i += PC_T) {
+            const C l = zmul(S[kk * R + i], inv);
+            S[kk * R + i] = l;
+            for (int j = kk + 1; j < nb; ++j) S[j * R + i] = zsub(S[j * R + i], zmul(l, s_prow[j]));
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nb * R; e += PC_T) {
+        const int j = e / R, i = e - j * R;
+        if (i < rn) A[(size_t)(j0 + j) * lda + r0 + i] = S[e];
+    }
+}
+
+// Workspace and launch geometry of the many-CTA panel for a block of n rows.
+template <class C>
+struct PanelCoop {
+    int G = 0;            // CTAs (at most one per SM)
+    C *rows = nullptr;    // [2][G][PC_NBMAX]
+    typename CReal<C>::R *val = nullptr;
+    int *pos = nullptr;
+    C *krow = nullptr;    // [2][PC_NBMAX]
+    GridBar *gb = nullptr;
+    void *buf = nullptr;
+};
+
+template <class C>
+static bool panel_coop_init(hm_handle_s *h, PanelCoop<C> &P)
+{
+    int dev = 0, nsm = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    P.G = nsm;
+    const size_t b_rows = sizeof(C) * 2 * (size_t)P.G * PC_NBMAX, b_val = sizeof(typename CReal<C>::R) * 2 * P.G;
+    const size_t b_pos = sizeof(int) * 2 * P.G, b_k = sizeof(C) * 2 * PC_NBMAX;
+    const size_t tot = b_rows + b_val + b_pos + b_k + sizeof(GridBar) + 64;
+    P.buf = dalloc(h, tot);
+    char *q = (char *)P.buf;
+    P.rows = (C *)q;
+    q += b_rows;
+    P.krow = (C *)q;
+    q += b_k;
+    P.val = (typename CReal<C>::R *)q;
+    q += b_val;
+    P.pos = (int *)q;
+    q += b_pos;
+    P.gb = (GridBar *)(((uintptr_t)q + 15) & ~(uintptr_t)15);
+    return true;
+}
+
+// Factor columns [j0, j0 + nb) over rows [j0, n) on G CTAs; nb and the slab height fit in
+// shared memory (checked by the caller through panel_width).
+template <class C>
+static void panel_coop(hm_handle_s *h, PanelCoop<C> &P, int n, C *A, int lda, int j0, int nb, int *piv, int *info)
+{
+    const int m = n - j0;
+    const int G = std::min(P.G, std::max(1, (m + 63) / 64));
+    const int R = (m + G - 1) / G;
+    const size_t smem = sizeof(C) * (size_t)nb * R;
+    static bool attr[2] = {false, false};
+    bool &a = attr[sizeof(C) == sizeof(cf) ? 0 : 1];
+    if (!a) {
+        HM_CUDA(cudaFuncSetAttribute(k_getf2_coop<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+        a = true;
+    }
+    HM_CUDA(cudaMemsetAsync(P.gb, 0, sizeof(GridBar), h->stream));
+    void *args[] = {(void *)&n, (void *)&A, (void *)&lda, (void *)&j0, (void *)&nb, (void *)&R, (void *)&piv,
+                    (void *)&info, (void *)&P.rows, (void *)&P.val, (void *)&P.pos, (void *)&P.krow, (void *)&P.gb};
+    HM_CUDA(cudaLaunchCooperativeKernel((const void *)k_getf2_coop<C>, dim3(G), dim3(PC_T), args, smem, h->stream));
+}
+
+// Columns of an inner panel step for a panel of m rows: the widest of 64, 32, 16 whose
+// slabs fit in 200 KB of shared memory on nsm CTAs; 0 when none does (one-CTA panel).
+template <class C>
+static int panel_width(int m, int nsm)
+{
+    const int G = std::min(nsm, std::max(1, (m + 63) / 64));
+    const size_t R = (size_t)((m + G - 1) / G);
+    for (int nb = PC_NBMAX; nb >= 16; nb /= 2)
+        if (sizeof(C) * nb * R <= 200 * 1024) return nb;
+    return 0;
+}
+
 // Row interchanges k <-> piv[k], k in [k0, k1), on the columns [0, c_lo) and [c_hi, n).
 template <class C>
 __global__ void k_laswp_range(C *A, int lda, int c_lo, int c_hi, int n, const int *piv, int k0, int k1)
@@ -502,13 +756,27 @@ void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
     C *work = nullptr;
     const bool inv12 = std::is_same<C, cf>::value && !h->prm.simt_gemm && n > 2 * LU_NBO;
     if (inv12) work = (C *)dalloc(h, sizeof(C) * ((size_t)LU_NBO * LU_NBO + (size_t)LU_NBO * (n - LU_NBO)));
+    // tall panels (at least PC_MIN_ROWS rows) factor on many CTAs
+    const int PC_MIN_ROWS = 2048;
+    PanelCoop<C> pc;
+    int nsm = 0;
+    if (n >= PC_MIN_ROWS) {
+        panel_coop_init<C>(h, pc);
+        nsm = pc.G;
+    }
     for (int J0 = 0; J0 < n; J0 += LU_NBO) {
         const int NB = std::min(LU_NBO, n - J0), REST = n - J0 - NB;
         PhaseScope ps_panel(h, PH_LU_PANEL);
-        for (int j0 = J0; j0 < J0 + NB; j0 += LU_NB) {
-            const int nb = std::min(LU_NB, J0 + NB - j0), rest = J0 + NB - j0 - nb;
-            k_getf2_panel<C><<<1, 512, 0, h->stream>>>(n, A, lda, j0, nb, piv, d_info);
-            HM_CHECK_LAUNCH();
+        const int wc = (n - J0 >= PC_MIN_ROWS) ? panel_width<C>(n - J0, nsm) : 0;
+        const int step = wc ? wc : LU_NB;
+        for (int j0 = J0; j0 < J0 + NB; j0 += step) {
+            const int nb = std::min(step, J0 + NB - j0), rest = J0 + NB - j0 - nb;
+            if (wc) {
+                panel_coop<C>(h, pc, n, A, lda, j0, nb, piv, d_info);
+            } else {
+                k_getf2_panel<C><<<1, 512, 0, h->stream>>>(n, A, lda, j0, nb, piv, d_info);
+                HM_CHECK_LAUNCH();
+            }
             const int ncols = NB - nb;  // the panel's other columns
             if (ncols > 0) {
                 k_laswp_range<C><<<(ncols + 127) / 128, 128, 0, h->stream>>>(A + (size_t)J0 * lda, lda, j0 - J0,
@@ -552,6 +820,7 @@ void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
         }
     }
     if (work) dfree(h, work);
+    if (pc.buf) dfree(h, pc.buf);
     h->flops_factor = saved;  // counted once above
 }
 

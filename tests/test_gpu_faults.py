@@ -4,8 +4,8 @@ Each injected fault must come back as its status code, and the handle must stay 
   * a zero pivot in a diagonal leaf -> HM_ERR_SINGULAR (H-LU, both precisions);
   * a NaN in the right-hand side -> HM_ERR_NUMERIC (scan of the solution);
   * a failed device allocation -> HM_ERR_OOM;
-  * non-finite or out-of-range inputs and formulations this library was built without ->
-    HM_ERR_ARG before any device work.
+  * non-finite or out-of-range inputs, out-of-range material parameters and formulations
+    this library was built without (the CFIE) -> HM_ERR_ARG before any device work.
 """
 import numpy as np
 import pytest
@@ -78,7 +78,8 @@ def test_bad_inputs_are_rejected_before_device_work():
     s = hm.Solver()
     bad = np.array(wl["bodies"], copy=True)
     bad[0, 0] = np.nan  # centre
-    cases = [dict(bodies=bad), dict(formulation=hm.HM_PEC_CFIE + 7), dict(formulation=hm.HM_DIEL_MULLER),
+    cases = [dict(bodies=bad), dict(formulation=hm.HM_PEC_CFIE + 7), dict(formulation=hm.HM_PEC_CFIE),
+             dict(formulation=hm.HM_DIEL_MULLER, eps_r=-1.0), dict(formulation=hm.HM_DIEL_MULLER, eps_r=2.0, mu_r=2.0),
              dict(quad_order=2), dict(quad_order=40),
              dict(trunc_tol=-1.0), dict(k0=np.inf)]
     for c in cases:

@@ -183,11 +183,12 @@ def test_matvec_against_dense_oracle():
 
 
 MID = {  # precision, factor_leaf, simt_gemm
-    "fp64": (hm.HM_FP64, 0, False),            # H-LU, dense blocks from 600-unknown clusters down
+    "fp64": (hm.HM_FP64, 640, False),          # H-LU, dense blocks from 600-unknown clusters down
     "fp64-dense": (hm.HM_FP64, 4800, False),   # one dense block, split into a group of 3 row tiles
     "fp32r": (hm.HM_FP32_REFINED, 0, False),   # adaptive: one dense block, tensor-core LU, 2 row tiles
     "fp32r-h": (hm.HM_FP32_REFINED, 640, False),  # H-LU above 600-unknown dense blocks, tensor-core products
-    "fp32r-simt": (hm.HM_FP32_REFINED, 0, True),  # CUDA-core products only, storage-chosen dense level
+    "fp64-adaptive": (hm.HM_FP64, 0, False),   # adaptive: the whole matrix as one dense block
+    "fp32r-simt": (hm.HM_FP32_REFINED, 0, True),  # CUDA-core products only, adaptive dense level
     "fp32r-fine": (hm.HM_FP32_REFINED, -1, False),  # the fill's leaves (leaf-level formatted arithmetic)
 }
 
