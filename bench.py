@@ -127,6 +127,8 @@ def cpu_baseline(wl, workload_name):
     import oracle
     if wl.get("formulation") == "MULLER":
         return None  # the row sampler of the oracle covers the MFIE system
+    if wl.get("independent"):
+        return None  # a batch of uncoupled bodies: the oracle holds one coupled system
     t0 = time.perf_counter()
     o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
     N = o.N
@@ -212,6 +214,7 @@ def run_reference(args, rank, world):
 def bench_config(args, wl):
     """The workload description both arms print (identical keys and values)."""
     return {"workload": args.workload, "formulation": wl.get("formulation", "MFIE"), "unknowns": wl_N(wl),
+            "bodies": len(wl["ms"]), "independent_bodies": bool(wl.get("independent", False)),
             "rhs": int(wl["kdirs"].shape[0]),
             "leaf": wl["leaf"], "eta": wl["eta"], "aca_tol": wl["aca_tol"],
             "l2": "working set (H-matrix, near store) > L2 between steps"}
@@ -227,6 +230,8 @@ def formulation_args(wl):
     from paper_2408_17116_gb300 import hm
     if wl.get("formulation") == "MULLER":
         return dict(formulation=hm.HM_DIEL_MULLER, eps_r=wl["eps_r"])
+    if wl.get("independent"):
+        return dict(independent=True)
     return {}
 
 
@@ -278,6 +283,36 @@ def one_step(s, wl, dirs, host=False, precision="fp32r"):
     return x, rcs
 
 
+def train_rank_model(s):
+    """Train the learned ACA-rank predictor on the ranks plain ACA reaches on four bodies
+    other than the bench workload (spheres and ellipsoids of 3.5-5 wavelengths, 4,800
+    unknowns each) and install it on the solver s (its fills then skip the attempts it
+    predicts to fail and size ACA buffers by its prediction; plain adaptive ACA re-runs any
+    under-predicted block)."""
+    import torch
+    from paper_2408_17116_gb300 import hm, workloads
+    t0 = time.perf_counter()
+    base = dict(load_workload("sphere_d8_m4_nc10"), ms=[2], nc=10)
+    bodies = [workloads.body(semi=(1.75,) * 3), workloads.body(semi=(2.5, 2.0, 1.5)),
+              workloads.body(semi=(2.25,) * 3), workloads.body(semi=(2.4, 1.6, 2.0))]
+    feats, targs = [], []
+    for bd in bodies:
+        t = hm.Solver()
+        t.hm_build_geometry(bd[None], base["ms"], base["nc"], base["k"], base["leaf"], base["eta"], base["aca_tol"])
+        t.hm_fill()
+        f, y = t.rank_samples()
+        feats.append(f)
+        targs.append(y)
+        t.close()
+    X, y = np.concatenate(feats), np.concatenate(targs)
+    m = hm.MLP(hm.RANK_NFEAT, 32)
+    m.set_params(workloads.mlp_init(hm.RANK_NFEAT, 32))
+    loss = m.train(torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"), 2000, 3e-3)
+    s.set_rank_model(m)
+    return {"trained_on": "4 bodies of 4,800 unknowns (spheres D = 3.5 and 4.5, ellipsoids)", "samples": int(len(y)),
+            "loss": loss, "r2": float(1.0 - loss / np.var(y)), "setup_s": time.perf_counter() - t0}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,6 +328,9 @@ def main():
                     help="skip the host-buffer end-to-end step (for kernel launch lists under a profiler)")
     ap.add_argument("--full-oracle", action="store_true",
                     help="with --impl reference: time the oracle's full dense fill, LU and solve once")
+    ap.add_argument("--rank-model", action="store_true",
+                    help="before the warm-up, train the ACA-rank MLP on four other bodies (4,800 unknowns "
+                         "each, not the bench workload) and let every fill of the run use it")
     ap.add_argument("--compare-workload", default=None,
                     help="workload of the FP32-refined vs plain-FP64 comparison, one step each "
                          "(default: the bench workload)")
@@ -331,6 +369,10 @@ def main():
         if rank == 0:
             print("[bench] %s" % msg, file=sys.stderr, flush=True)
 
+    rank_info = None
+    if args.rank_model:
+        rank_info = train_rank_model(s)
+        progress("rank model: %s" % json.dumps(rank_info))
     for i in range(args.warmup):
         t = time.perf_counter()
         one_step(s, wl, dirs, precision=prec)
@@ -440,6 +482,8 @@ def main():
            "e2e": ({"value": N / e2e_s, "unit": "unknowns/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "wall_s": e2e_s} if e2e_s else None),
            "roofline": roof, "kernels": cands[1:]}
+    if rank_info is not None:
+        out["rank_model"] = dict(rank_info, aca_skipped=s.hm_query("ACA_SKIPPED"), aca_reruns=s.hm_query("ACA_RERUNS"))
     if not args.no_compare:
         # FP32 H-LU + FP64 refinement against the plain FP64 H-LU on the same GPU, one timed
         # step each, with each solution's error against the stored dense-oracle solution

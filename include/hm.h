@@ -103,6 +103,11 @@ typedef struct {
     int simt_gemm;        /* HM_FP32_REFINED: nonzero keeps every complex64 product of the H-LU on the
                              CUDA cores; 0 runs the large ones on the tensor cores (tcgen05, operands
                              split into two BF16 parts, three products accumulated in FP32) */
+    int independent;      /* nonzero: the bodies do not interact -- each scatters the incident waves alone
+                             (a batch of scatterers).  The system is block diagonal, one block per body:
+                             clusters never mix bodies, blocks between bodies are zero (no ACA), near pairs
+                             stay within a body, and the factor stores each body's diagonal block dense
+                             (factor_leaf 0).  One fill, factor and solve serve the whole batch. */
 } hm_params;
 
 /* One cube-mapped ellipsoid: 6 m^2 curvilinear patches r = center + rot diag(semi) c/|c|,
@@ -161,7 +166,8 @@ enum {
     HM_Q_KCORE_SECONDS = 37,  /* core factorisation: pivoted QR (complex64) or Jacobi SVD (complex128) */
     HM_Q_KCORE_FLOPS = 38,    /* counted for the pivoted QR only (the Jacobi sweep count varies) */
     HM_Q_KCORE_LAUNCHES = 39,
-    HM_Q_DENSE_LEVEL = 40, /* cluster level from which the last hm_factor stored dense blocks (-1: none) */
+    HM_Q_DENSE_LEVEL = 40, /* cluster level from which the last hm_factor stored dense blocks (-1: none;
+                              -2: each body's diagonal block, independent bodies) */
     /* products of at least 1e9 real flops in the last hm_factor (the dense Schur updates), device
      * time from CUDA events around each launch, their algorithmic real flops and count: */
     HM_Q_KGEMM_SECONDS = 41,

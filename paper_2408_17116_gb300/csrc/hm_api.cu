@@ -115,8 +115,9 @@ void free_all(hm_handle_s *h)
     h->leaves.clear();
     h->root = nullptr;
     void *ptrs[] = {h->d_bodies, h->d_patches, h->d_nodes, h->d_pair_q, h->d_pair_p, h->d_nearidx,
-                    h->d_near,   h->d_perm,    h->d_iperm, h->d_d1};
+                    h->d_near,   h->d_perm,    h->d_iperm, h->d_d1,     h->d_patch_body};
     for (void *p : ptrs) dfree(h, p);
+    h->d_patch_body = nullptr;
     h->d_bodies = nullptr;
     h->d_patches = nullptr;
     h->d_nodes = nullptr;
@@ -205,7 +206,7 @@ void rank_features(hm_handle_s *h, const Block *b, float *f)
 // size: the factor with dense 2,400-unknown blocks takes 3.4 s, with dense 600-unknown
 // blocks and low-rank blocks above them 13 s, recompressions dominating the latter.)
 template <class Z>
-static int dense_level(hm_handle_s *h, BlockT<Z> *root)
+static int dense_level(hm_handle_s *h, BlockT<Z> *root, bool c64)
 {
     if (h->prm.factor_leaf < 0) return -1;
     auto level_of = [&](int bd) {
@@ -214,6 +215,7 @@ static int dense_level(hm_handle_s *h, BlockT<Z> *root)
         return lev;
     };
     if (h->prm.factor_leaf > 0) return level_of(h->prm.factor_leaf);
+    if (h->prm.independent) return HM_MERGE_BODIES;  // each body's diagonal block, dense
     // A dense block factors at the rate of large products (tensor cores for complex64, the
     // FP64 pipe at its peak for complex128) while the formatted arithmetic below it runs
     // small, latency-bound kernels: merge from the coarsest level whose dense storage fits
@@ -221,12 +223,12 @@ static int dense_level(hm_handle_s *h, BlockT<Z> *root)
     // clusters of at most 24,576 unknowns (a dense FP64 LU of that size takes seconds).
     size_t fr = 0, tot = 0;
     HM_CUDA(cudaMemGetInfo(&fr, &tot));
-    const int Lm = dense_level_by_memory<Z>(h, root, 0.4 * (double)fr / sizeof(Z));
+    const int Lm = dense_level_by_memory<Z>(h, root, 0.4 * (double)fr / (c64 ? sizeof(cf) : sizeof(zc)));
     if (Lm >= 0) {
-        if (sizeof(Z) == sizeof(cf) && !h->prm.simt_gemm) return Lm;
+        if (c64 && !h->prm.simt_gemm) return Lm;
         return std::max(Lm, level_of(24576));
     }
-    const int cap = sizeof(Z) == sizeof(cf) ? 4096 : 1280;
+    const int cap = c64 ? 4096 : 1280;
     const int L = dense_level_by_storage<Z>(h, root, cap, 0.35);
     return L >= 0 ? L : level_of(640);
 }
@@ -442,7 +444,7 @@ hm_status hm_fill(hm_handle h)
             Timer t(h->stream);
             std::vector<Block *> pending;
             for (Block *b : h->leaves)
-                if (b->type == B_LR) pending.push_back(b);
+                if (b->type == B_LR && !b->zero) pending.push_back(b);
             int cap = h->prm.aca_max_rank > 0 ? h->prm.aca_max_rank : HM_DEFAULT_RANK_CAP;
             h->aca_nonconv = 0;
             h->aca_reruns = 0;
@@ -638,15 +640,16 @@ hm_status hm_factor(hm_handle h)
             h->tfac32 = nullptr;
             free_tree(h, h->blocks32);
             h->dirty32.clear();
-            h->root32 = clone_tree<cf>(h, h->root, h->blocks32);
-            // with tensor-core products the dense level does not depend on the ranks: merge
-            // first, so that only the low-rank leaves that stay are recompressed
+            // with tensor-core products the dense level does not depend on the ranks: the copy
+            // is made with its dense blocks already merged (one batched expansion), and only
+            // the low-rank leaves that stay are recompressed
             const bool merge_first = !h->prm.simt_gemm && h->prm.factor_leaf >= 0;
             int lev = -1;
-            if (merge_first) {
-                lev = dense_level<cf>(h, h->root32);
-                if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
-            }
+            if (merge_first) lev = dense_level<zc>(h, h->root, true);
+            if (lev != -1)
+                h->root32 = clone_tree_merged(h, h->root, lev, h->blocks32);
+            else
+                h->root32 = clone_tree<cf>(h, h->root, h->blocks32);
             // the factor only needs factor_tol: recompress the copied low-rank leaves
             std::vector<Block32 *> lr;
             std::vector<int> ranks;
@@ -657,8 +660,8 @@ hm_status hm_factor(hm_handle h)
                 }
             batched_truncate<cf>(h, lr, ranks, h->factor_tol);
             if (!merge_first) {
-                lev = dense_level<cf>(h, h->root32);
-                if (lev >= 0) coarsen_tree<cf>(h, h->root32, lev);
+                lev = dense_level<cf>(h, h->root32, true);
+                if (lev != -1) coarsen_tree<cf>(h, h->root32, lev);
             }
             h->dense_lev = lev;
             if (zero_pivot) {  // host-side injection: the first column of the first leaf is zero
@@ -683,8 +686,8 @@ hm_status hm_factor(hm_handle h)
         }
         Timer t(h->stream);
         h->dirty64.clear();
-        const int lev = dense_level<zc>(h, h->root);
-        if (lev >= 0) {
+        const int lev = dense_level<zc>(h, h->root, false);
+        if (lev != -1) {
             coarsen_tree<zc>(h, h->root, lev);
             rebuild_leaves(h);
         }

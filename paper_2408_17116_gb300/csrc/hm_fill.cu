@@ -16,6 +16,7 @@ struct EntryCtx {
     int nc;
     MullerMedia md;       // N-Mueller: the interior medium
     const double *d1;     // N-Mueller: [nc][nc] derivatives of the cardinal functions at the nodes
+    const int *patch_body;  // independent bodies: body of each patch (entries between bodies are zero)
 };
 
 // The four entries A[2ni + b, 2nj + a] of node pair (ni, nj) (natural node indices),
@@ -90,6 +91,10 @@ __device__ __forceinline__ void node_pair_muller(const EntryCtx &E, int ni, int 
 // dof x dof entries of node pair (ni, nj), out[b * dof + a]
 __device__ __forceinline__ void pair_entries(const EntryCtx &E, int ni, int nj, zc *out)
 {
+    if (E.patch_body && E.patch_body[ni / E.nc2] != E.patch_body[nj / E.nc2]) {
+        for (int e = 0; e < E.dof * E.dof; ++e) out[e] = zmake(0, 0);
+        return;
+    }
     if (E.dof == 4)
         node_pair_muller(E, ni, nj, out);
     else
@@ -111,6 +116,7 @@ static EntryCtx entry_ctx(hm_handle_s *h)
     E.near = h->d_near;
     E.perm = h->d_perm;
     E.k = h->prm.k0;
+    E.patch_body = h->d_patch_body;
     return E;
 }
 

@@ -546,6 +546,7 @@ BlockT<Z> *clone_tree(hm_handle_s *h, Block *b, std::vector<BlockT<Z> *> &owned)
     c->t = b->t;
     c->s = b->s;
     c->k = b->k;
+    c->zero = b->zero;
     c->leaf_id = b->leaf_id;
     if (b->type == B_DENSE) {
         c->D = zalloc<Z>(h, (size_t)b->nr * b->nc);
@@ -561,6 +562,157 @@ BlockT<Z> *clone_tree(hm_handle_s *h, Block *b, std::vector<BlockT<Z> *> &owned)
         for (int i = 0; i < 4; ++i) c->ch[i] = clone_tree<Z>(h, b->ch[i], owned);
     }
     return c;
+}
+
+// ---------------------------------------------------------------------------
+// Complex64 copy of the FP64 tree with every hierarchical block on cluster level `level`
+// or deeper stored as one dense block, written directly from the FP64 leaves below it by
+// one batched launch: one CTA per 64 x 64 tile of a leaf (dense leaves converted, low-rank
+// leaves expanded as U V^H in FP32 from the converted factors).
+// ---------------------------------------------------------------------------
+struct ExpandJob {
+    const zc *D, *U, *V;  // FP64 leaf: dense (D) or low-rank (U, V, rank k)
+    int nr, nc, k;
+    int i0, j0;           // tile origin inside the leaf
+    cf *dst;              // the leaf's top-left entry in the dense block
+    int ld;
+};
+
+#define EX_T 256
+#define EX_KC 32
+
+__global__ void __launch_bounds__(EX_T) k_expand(const ExpandJob *__restrict__ jobs)
+{
+    const ExpandJob J = jobs[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int mi = min(64, J.nr - J.i0), mj = min(64, J.nc - J.j0);
+    if (!J.U) {
+        for (int e = tid; e < 64 * 64; e += EX_T) {
+            const int ii = e & 63, jj = e >> 6;
+            if (ii < mi && jj < mj) {
+                const zc v = J.D ? J.D[(size_t)(J.j0 + jj) * J.nr + J.i0 + ii] : zmake(0, 0);
+                J.dst[(size_t)(J.j0 + jj) * J.ld + J.i0 + ii] = make_float2((float)v.x, (float)v.y);
+            }
+        }
+        return;
+    }
+    __shared__ cf Us[EX_KC][64], Vs[EX_KC][65];
+    const int tx = tid & 15, ty = tid >> 4;  // outputs (tx + 16 a, ty + 16 b)
+    cf acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int p0 = 0; p0 < J.k; p0 += EX_KC) {
+        const int kc = min(EX_KC, J.k - p0);
+        __syncthreads();
+        for (int e = tid; e < EX_KC * 64; e += EX_T) {
+            const int r = e & 63, q = e >> 6;
+            zc u = zmake(0, 0), v = zmake(0, 0);
+            if (q < kc && r < mi) u = J.U[(size_t)(p0 + q) * J.nr + J.i0 + r];
+            if (q < kc && r < mj) v = J.V[(size_t)(p0 + q) * J.nc + J.j0 + r];
+            Us[q][r] = make_float2((float)u.x, (float)u.y);
+            Vs[q][r] = make_float2((float)v.x, (float)-v.y);  // conj(V)
+        }
+        __syncthreads();
+        for (int q = 0; q < kc; ++q) {
+            cf ua[4], vb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) ua[a] = Us[q][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) vb[b] = Vs[q][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = zfma(ua[a], vb[b], acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int ii = tx + 16 * a, jj = ty + 16 * b;
+            if (ii < mi && jj < mj) J.dst[(size_t)(J.j0 + jj) * J.ld + J.i0 + ii] = acc[a][b];
+        }
+}
+
+static void expand_jobs(const Block *b, cf *D, int ld, int r0, int c0, std::vector<ExpandJob> &jobs)
+{
+    if (b->type == B_HIER) {
+        for (int i = 0; i < 4; ++i) expand_jobs(b->ch[i], D, ld, r0, c0, jobs);
+        return;
+    }
+    ExpandJob J;
+    J.D = b->type == B_DENSE ? b->D : nullptr;
+    J.U = b->type == B_LR && b->k ? b->U : nullptr;
+    J.V = b->type == B_LR && b->k ? b->V : nullptr;
+    J.nr = b->nr;
+    J.nc = b->nc;
+    J.k = b->type == B_LR ? b->k : 0;
+    J.dst = D + (size_t)(b->c0 - c0) * ld + (b->r0 - r0);
+    J.ld = ld;
+    for (int i0 = 0; i0 < b->nr; i0 += 64)
+        for (int j0 = 0; j0 < b->nc; j0 += 64) {
+            J.i0 = i0;
+            J.j0 = j0;
+            jobs.push_back(J);
+        }
+}
+
+static Block32 *clone_merged_rec(hm_handle_s *h, Block *b, int level, std::vector<Block32 *> &owned,
+                                 std::vector<ExpandJob> &jobs)
+{
+    Block32 *c = new Block32();
+    owned.push_back(c);
+    c->type = b->type;
+    c->r0 = b->r0;
+    c->nr = b->nr;
+    c->c0 = b->c0;
+    c->nc = b->nc;
+    c->t = b->t;
+    c->s = b->s;
+    c->k = b->k;
+    c->zero = b->zero;
+    c->leaf_id = b->leaf_id;
+    if (b->type == B_HIER && merges_at(h, b, level)) {
+        c->type = B_DENSE;
+        c->k = 0;
+        c->D = zalloc<cf>(h, (size_t)b->nr * b->nc);
+        expand_jobs(b, c->D, b->nr, b->r0, b->c0, jobs);
+    } else if (b->type == B_DENSE) {
+        c->D = zalloc<cf>(h, (size_t)b->nr * b->nc);
+        convert_vec(h, b->D, c->D, (size_t)b->nr * b->nc);
+    } else if (b->type == B_LR) {
+        if (b->k) {
+            c->U = zalloc<cf>(h, (size_t)b->nr * b->k);
+            c->V = zalloc<cf>(h, (size_t)b->nc * b->k);
+            convert_vec(h, b->U, c->U, (size_t)b->nr * b->k);
+            convert_vec(h, b->V, c->V, (size_t)b->nc * b->k);
+        }
+    } else {
+        for (int i = 0; i < 4; ++i) c->ch[i] = clone_merged_rec(h, b->ch[i], level, owned, jobs);
+    }
+    return c;
+}
+
+Block32 *clone_tree_merged(hm_handle_s *h, Block *root, int level, std::vector<Block32 *> &owned)
+{
+    std::vector<ExpandJob> jobs;
+    Block32 *r = clone_merged_rec(h, root, level, owned, jobs);
+    // one launch per 2^20 tiles (grid limit headroom)
+    const size_t CH = (size_t)1 << 20;
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += CH) {
+        const size_t nj = std::min(CH, jobs.size() - j0);
+        ExpandJob *d = (ExpandJob *)dalloc(h, sizeof(ExpandJob) * nj);
+        HM_CUDA(cudaMemcpyAsync(d, jobs.data() + j0, sizeof(ExpandJob) * nj, cudaMemcpyHostToDevice, h->stream));
+        k_expand<<<(unsigned)nj, EX_T, 0, h->stream>>>(d);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+        dfree(h, d);
+    }
+    // the host job list must outlive the asynchronous copies
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    return r;
 }
 
 template <class Z>
@@ -618,11 +770,20 @@ static void release_subtree(hm_handle_s *h, BlockT<Z> *b)
 // keep their format, so every block row of the dense level holds dense blocks or whole
 // low-rank blocks of that level and above, and the partial pivoting of a dense diagonal
 // block stays within its own rows.
+// Whether the hierarchical block b becomes one dense block at the given merge level:
+// clusters on that level or deeper, or (HM_MERGE_BODIES) the diagonal block of one body.
+template <class Z>
+bool merges_at(const hm_handle_s *h, const BlockT<Z> *b, int level)
+{
+    if (level == HM_MERGE_BODIES) return b->t == b->s && h->clusters[b->t].body_root;
+    return h->clusters[b->t].level >= level;
+}
+
 template <class Z>
 void coarsen_tree(hm_handle_s *h, BlockT<Z> *b, int level)
 {
     if (b->type != B_HIER) return;
-    if (h->clusters[b->t].level >= level) {
+    if (merges_at(h, b, level)) {
         Z *D = (Z *)dalloc(h, sizeof(Z) * (size_t)b->nr * b->nc);
         for (int i = 0; i < 4; ++i) expand_into(h, b->ch[i], D, b->nr, b->r0, b->c0);
         for (int i = 0; i < 4; ++i) {
@@ -697,6 +858,7 @@ int dense_level_by_memory(hm_handle_s *h, BlockT<Z> *root, double budget_words)
     template BlockT<Z> *clone_tree<Z>(hm_handle_s *, Block *, std::vector<BlockT<Z> *> &);         \
     template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);                         \
     template void coarsen_tree<Z>(hm_handle_s *, BlockT<Z> *, int);                                \
+    template bool merges_at<Z>(const hm_handle_s *, const BlockT<Z> *, int);                       \
     template int dense_level_by_storage<Z>(hm_handle_s *, BlockT<Z> *, int, double);              \
     template int dense_level_by_memory<Z>(hm_handle_s *, BlockT<Z> *, double);
 HM_INST_HLU(zc)

@@ -41,6 +41,8 @@ struct Cluster {
     double bmin[3], bmax[3];
     int child[2];
     int level;
+    int b0 = 0, b1 = 0;      // bodies of its nodes: [b0, b1] (independent bodies: contiguous)
+    bool body_root = false;  // independent bodies: the cluster of one whole body
 };
 
 enum BType { B_DENSE = 0, B_LR = 1, B_HIER = 2 };
@@ -62,6 +64,7 @@ struct BlockT {
     std::vector<C *> pu, pv;
     std::vector<int> pk;
     int pend_k = 0;
+    bool zero = false;      // independent bodies: a block between two bodies (identically zero)
     bool dirty = false;     // queued for the next batched recompression
     bool in_batch = false;  // scratch flag while a batch is assembled
 };
@@ -114,6 +117,8 @@ struct hm_handle_s {
     std::vector<int> pair_q, pair_p;  // per pair
     int *d_pair_q = nullptr, *d_pair_p = nullptr;
     int *d_nearidx = nullptr;  // [P][P] -> pair index or -1
+    int *d_patch_body = nullptr;  // independent bodies: body of each patch (device), else null
+    std::vector<int> node_body;   // body of each node (natural order, host)
     zc *d_near = nullptr;      // [npairs][dof nc^2][dof nc^2]
     double *d_d1 = nullptr;    // [nc][nc] derivatives of the cardinal functions at the nodes (N-Mueller)
     unsigned long long *d_counter = nullptr;  // device counters (quadrature points)
@@ -308,9 +313,17 @@ template <class C>
 BlockT<C> *clone_tree(hm_handle_s *h, Block *b, std::vector<BlockT<C> *> &owned);
 template <class C>
 void free_tree(hm_handle_s *h, std::vector<BlockT<C> *> &owned);
+// Complex64 copy of the FP64 tree with every hierarchical block on cluster level `level` or
+// deeper already merged into one dense block (one batched expansion launch).
+Block32 *clone_tree_merged(hm_handle_s *h, Block *root, int level, std::vector<Block32 *> &owned);
 // Merge every hierarchical block on cluster level `level` or deeper into one dense block.
 template <class C>
 void coarsen_tree(hm_handle_s *h, BlockT<C> *root, int level);
+// level value of coarsen_tree / clone_tree_merged: merge the diagonal block of every body
+// (independent bodies)
+#define HM_MERGE_BODIES (-2)
+template <class C>
+bool merges_at(const hm_handle_s *h, const BlockT<C> *b, int level);
 // Coarsest level of clusters of at most cap unknowns whose non-low-rank blocks store at
 // least theta of their dense size (-1: none).
 template <class C>

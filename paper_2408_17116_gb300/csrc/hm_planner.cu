@@ -96,10 +96,34 @@ static void build_clusters(hm_handle_s *h, int off, int cnt, int level, int dept
             c.bmax[d] = std::max(c.bmax[d], X[d * n + nd]);
         }
     }
+    const bool indep = h->prm.independent && !h->node_body.empty();
+    if (indep) {
+        c.b0 = h->node_body[h->perm_node[off]];
+        c.b1 = h->node_body[h->perm_node[off + cnt - 1]];
+    }
     int me = (int)h->clusters.size();
     h->clusters.push_back(c);
     idx_out = me;
-    if (level >= depth || cnt < 2) return;
+    if (indep && c.b0 != c.b1) {
+        // several bodies (contiguous in tree order): split at the body boundary nearest the
+        // middle, so that every cluster below holds one body
+        int best = -1;
+        for (int i = off + 1; i < off + cnt; ++i)
+            if (h->node_body[h->perm_node[i]] != h->node_body[h->perm_node[i - 1]] &&
+                (best < 0 || std::abs(2 * (i - off) - cnt) < std::abs(2 * (best - off) - cnt)))
+                best = i;
+        int c0, c1;
+        build_clusters(h, off, best - off, level + 1, depth, c0);
+        build_clusters(h, best, off + cnt - best, level + 1, depth, c1);
+        h->clusters[me].child[0] = c0;
+        h->clusters[me].child[1] = c1;
+        h->clusters[c0].body_root = h->clusters[c0].b0 == h->clusters[c0].b1;
+        h->clusters[c1].body_root = h->clusters[c1].b0 == h->clusters[c1].b1;
+        return;
+    }
+    // one body: geometric bisection; independent bodies stop at n_leaf unknowns per cluster,
+    // otherwise at the common leaf depth
+    if (indep ? (h->dof * cnt <= h->prm.leaf || cnt < 2) : (level >= depth || cnt < 2)) return;
     int ax = 0;
     double ext = -1;
     for (int d = 0; d < 3; ++d)
@@ -131,6 +155,15 @@ static Block *build_blocks(hm_handle_s *h, int t, int s)
     b->nr = h->dof * ct.cnt;
     b->c0 = h->dof * cs.off;
     b->nc = h->dof * cs.cnt;
+    if (h->prm.independent && (ct.b1 < cs.b0 || cs.b1 < ct.b0)) {
+        // independent bodies: no body in common, an identically zero block
+        b->type = B_LR;
+        b->zero = true;
+        b->k = 0;
+        b->leaf_id = (int)h->leaves.size();
+        h->leaves.push_back(b);
+        return b;
+    }
     double dist = bbox_dist(ct.bmin, ct.bmax, cs.bmin, cs.bmax);
     double dm = std::min(bbox_diam(ct.bmin, ct.bmax), bbox_diam(cs.bmin, cs.bmax));
     bool adm = dist > 0.0 && dm <= h->prm.eta * dist;
@@ -208,6 +241,7 @@ void plan_geometry(hm_handle_s *h)
         for (int p = 0; p < P; ++p) {
             bool nr = (q == p) || bbox_dist(&bmin[3 * q], &bmax[3 * q], &bmin[3 * p], &bmax[3 * p]) <
                                       h->prm.near_delta * std::max(diam[q], diam[p]);
+            if (h->prm.independent && h->patches[q].body != h->patches[p].body) nr = false;
             if (nr) {
                 nearidx[(size_t)q * P + p] = (int)h->pair_q.size();
                 h->pair_q.push_back(q);
@@ -221,6 +255,16 @@ void plan_geometry(hm_handle_s *h)
     HM_CUDA(cudaMemcpyAsync(h->d_nearidx, nearidx.data(), sizeof(int) * nearidx.size(), cudaMemcpyHostToDevice, h->stream));
     HM_CUDA(cudaMemcpyAsync(h->d_pair_q, h->pair_q.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, h->stream));
     HM_CUDA(cudaMemcpyAsync(h->d_pair_p, h->pair_p.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, h->stream));
+    h->node_body.clear();
+    if (h->prm.independent) {
+        h->node_body.resize(h->nnode);
+        for (int nd = 0; nd < h->nnode; ++nd) h->node_body[nd] = h->patches[nd / nc2].body;
+        std::vector<int> pb(P);
+        for (int p = 0; p < P; ++p) pb[p] = h->patches[p].body;
+        h->d_patch_body = (int *)dalloc(h, sizeof(int) * P);
+        HM_CUDA(cudaMemcpyAsync(h->d_patch_body, pb.data(), sizeof(int) * P, cudaMemcpyHostToDevice, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));  // pb is a host temporary
+    }
     build_cluster_tree(h);
     std::vector<int> perm(h->N), iperm(h->N);
     for (int pos = 0; pos < h->nnode; ++pos)
@@ -249,6 +293,7 @@ void build_cluster_tree(hm_handle_s *h)
     h->clusters.clear();
     int root;
     build_clusters(h, 0, h->nnode, 0, depth, root);
+    h->clusters[root].body_root = h->prm.independent && h->clusters[root].b0 == h->clusters[root].b1;
 }
 
 extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int leaf, double eta, int *nblocks,

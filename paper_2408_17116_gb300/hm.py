@@ -46,7 +46,7 @@ class hm_params(ctypes.Structure):
                 ("factor_tol", ctypes.c_double), ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int),
                 ("cfie_alpha", ctypes.c_double), ("eps_r_re", ctypes.c_double), ("eps_r_im", ctypes.c_double),
                 ("mu_r", ctypes.c_double), ("trunc_tol", ctypes.c_double), ("quad_order", ctypes.c_int),
-                ("factor_leaf", ctypes.c_int), ("simt_gemm", ctypes.c_int)]
+                ("factor_leaf", ctypes.c_int), ("simt_gemm", ctypes.c_int), ("independent", ctypes.c_int)]
 
 
 class hm_body(ctypes.Structure):
@@ -240,7 +240,7 @@ class Solver:
     def hm_build_geometry(self, bodies, ms, nc, k0, leaf, eta, aca_tol, near_delta=0.5, aca_max_rank=0,
                           keep_matrix=False, precision=HM_FP64, factor_tol=0.0, refine_tol=0.0, refine_max_iter=0,
                           formulation=HM_PEC_MFIE, cfie_alpha=0.0, eps_r=1.0, mu_r=0.0, trunc_tol=0.0,
-                          quad_order=0, factor_leaf=0, simt_gemm=False):
+                          quad_order=0, factor_leaf=0, simt_gemm=False, independent=False):
         self._bodies = make_bodies(bodies, ms)
         eps = complex(eps_r)
         p = hm_params(k0=float(k0), formulation=int(formulation), leaf=int(leaf), eta=float(eta),
@@ -249,7 +249,7 @@ class Solver:
                       refine_tol=float(refine_tol), refine_max_iter=int(refine_max_iter),
                       cfie_alpha=float(cfie_alpha), eps_r_re=eps.real, eps_r_im=eps.imag, mu_r=float(mu_r),
                       trunc_tol=float(trunc_tol), quad_order=int(quad_order), factor_leaf=int(factor_leaf),
-                      simt_gemm=int(bool(simt_gemm)))
+                      simt_gemm=int(bool(simt_gemm)), independent=int(bool(independent)))
         self._check(self.L.hm_build_geometry(self.h, self._bodies, len(ms), int(nc), ctypes.byref(p)))
         self.N = int(self.hm_query("N"))
         self.dof = 4 if int(formulation) == HM_DIEL_MULLER else 2

@@ -77,11 +77,40 @@ def workload(name):
         kh, pol = axial_incidence()
         return dict(name=name, bodies=body(semi=(0.5,) * 3)[None], ms=[2], nc=12, k=K0, leaf=96, eta=2.0,
                     aca_tol=1e-8, kdirs=kh, pols=pol, radius=0.5, formulation="MULLER", eps_r=80.0)
+    if name == "batch_spheroids64":  # 64 independent PEC prolate spheroids, 16 incidences each
+        bodies, ms = spheroid_batch(64, SEED + 3)
+        kh, pol = incidence(16, SEED + 4)
+        return dict(name=name, bodies=bodies, ms=ms, nc=8, k=K0, leaf=64, eta=2.0, aca_tol=1e-7, kdirs=kh,
+                    pols=pol, independent=True)
+    if name == "batch_spheroids3":  # three independent spheroids (test batch), 2 incidences
+        bodies, ms = spheroid_batch(3, SEED + 5, major=(1.0, 1.6, 2.0))
+        kh, pol = incidence(2, SEED + 6)
+        return dict(name=name, bodies=bodies, ms=ms, nc=8, k=K0, leaf=64, eta=2.0, aca_tol=1e-7, kdirs=kh,
+                    pols=pol, independent=True)
     raise KeyError(name)
 
 
+def spheroid_batch(n, seed, major=None):
+    """n prolate spheroids along z: axis ratio ~ U[1, 3], major diameter ~ U[1, 4] wavelengths
+    (or the given diameters), m = 1, 2, 3 patches per cube edge for a major diameter below
+    4/3, below 8/3, else (768 to 6,912 unknowns at 8 x 8 nodes); centres on a cubic grid
+    of 6-wavelength spacing.  Returns (bodies[n, 15], ms[n])."""
+    g = np.random.Generator(np.random.Philox(seed))
+    ratio = 1.0 + 2.0 * g.random(n)
+    dmaj = 1.0 + 3.0 * g.random(n) if major is None else np.asarray(major, float)
+    side = int(np.ceil(n ** (1.0 / 3.0)))
+    bodies, ms = [], []
+    for i in range(n):
+        c = 6.0 * np.array([i % side, (i // side) % side, i // (side * side)], float)
+        a = 0.5 * dmaj[i]
+        b = a / ratio[i]
+        bodies.append(body(center=c, semi=(b, b, a)))
+        ms.append(1 if dmaj[i] < 4.0 / 3.0 else (2 if dmaj[i] < 8.0 / 3.0 else 3))
+    return np.stack(bodies), ms
+
+
 WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d4_m2_nc10", "sphere_d2_m2_nc6", "ellipsoid_small",
-             "dielectric_d1_eps80_m2_nc12")
+             "dielectric_d1_eps80_m2_nc12", "batch_spheroids64", "batch_spheroids3")
 
 
 def mlp_init(nin, nh, seed=SEED):
