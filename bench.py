@@ -328,9 +328,10 @@ def main():
                     help="skip the host-buffer end-to-end step (for kernel launch lists under a profiler)")
     ap.add_argument("--full-oracle", action="store_true",
                     help="with --impl reference: time the oracle's full dense fill, LU and solve once")
-    ap.add_argument("--rank-model", action="store_true",
-                    help="before the warm-up, train the ACA-rank MLP on four other bodies (4,800 unknowns "
-                         "each, not the bench workload) and let every fill of the run use it")
+    ap.add_argument("--no-rank-model", action="store_true",
+                    help="plain adaptive ACA: do not train and use the learned ACA-rank predictor (by default "
+                         "it is trained before the warm-up on four other bodies of 4,800 unknowns, not the "
+                         "bench workload, and every fill of the run uses it)")
     ap.add_argument("--compare-workload", default=None,
                     help="workload of the FP32-refined vs plain-FP64 comparison, one step each "
                          "(default: the bench workload)")
@@ -370,7 +371,7 @@ def main():
             print("[bench] %s" % msg, file=sys.stderr, flush=True)
 
     rank_info = None
-    if args.rank_model:
+    if not args.no_rank_model:
         rank_info = train_rank_model(s)
         progress("rank model: %s" % json.dumps(rank_info))
     for i in range(args.warmup):

@@ -283,6 +283,13 @@ hm_status hm_get_trunc_log_host(hm_handle h, int *nbatches, double *out);
 hm_status hm_cgemm(hm_handle h, char opA, char opB, int m, int n, int k, const float *alpha, const void *A, int lda,
                    const void *B, int ldb, const float *beta, void *C, int ldc, int path);
 
+/* The stage-count autotuner of the tensor-core products (process-wide): for each depth class
+ * c = 0..7 (packed depth 64 << c), stages[c] = the pipeline depth chosen (2: two CTAs per SM,
+ * 4: one CTA per SM; 0: not tuned yet) and ms[2c], ms[2c + 1] the best of three timed
+ * launches of the 2- and the 4-stage variant on the class's first large product (a leading
+ * block of at most 4096 x 4096 complex outputs, into scratch memory).  No GPU work. */
+hm_status hm_tc_tuning(int *stages, float *ms);
+
 /* Host-side fault injection for tests of the error paths (the paper has no counterpart).
  * Arms one fault for the next call that reaches it; no GPU fault, trap or hang is caused.
  *   HM_FAULT_ZERO_PIVOT: hm_factor zeroes the first column of the first diagonal leaf before

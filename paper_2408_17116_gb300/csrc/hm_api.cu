@@ -1069,6 +1069,13 @@ hm_status hm_cgemm(hm_handle h, char opA, char opB, int m, int n, int k, const f
     });
 }
 
+hm_status hm_tc_tuning(int *stages, float *ms)
+{
+    if (!stages || !ms) return HM_ERR_ARG;
+    tc_tune_record(stages, ms);
+    return HM_OK;
+}
+
 hm_status hm_inject_fault(hm_handle h, int what)
 {
     return guard(h, [&] {

@@ -241,6 +241,9 @@ template <class C>
 void ztrsm_luh(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X);  // X = U^-H X
 template <class C>
 void ztrsm_run(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X);  // X = X U^-1 (X rows x n)
+// Li = L^-1, Ui = U^-1 (n x n, ld n) of the LU factors stored in T (unit lower L, upper U)
+template <class C>
+void ztri_inverses(hm_handle_s *h, const C *T, int ldt, int n, C *Li, C *Ui);
 template <class C>
 void zcopy2d(hm_handle_s *h, MVT<C> dst, MVT<C> src);
 template <class C>
@@ -294,6 +297,7 @@ bool tc_eligible(const hm_handle_s *h, int m, int n, int k);
 void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, const cf *A, int lda, const cf *B,
              int ldb, cf beta, cf *Cm, int ldc);
 void tc_check(hm_handle_s *h);  // after a synchronisation: HM_ERR_TIMEOUT if a pipeline wait expired
+void tc_tune_record(int *stages, float *ms2);  // the stage-count autotuner's choices and timings
 
 // ---- hm_io.cu ----
 void launch_rhs(hm_handle_s *h, int nrhs, const double *d_dirs, zc *d_b);  // tree order

@@ -975,6 +975,36 @@ void ztrsm_luh(hm_handle_s *h, const C *U, int ldu, int n, MVT<C> X)
     }
 }
 
+// Explicit inverses of the triangular factors of a diagonal block: Li = L^-1 (unit lower)
+// and Ui = U^-1 (upper), n x n with ld n, L and U read from T (ld ldt).  Blocked substitution
+// on the identity restricted to the columns that can be nonzero: row block b of L^-1 has
+// nonzeros only in columns [0, b1), row block b of U^-1 only in columns [b0, n) (half the
+// work of a solve against the full identity).
+template <class C>
+void ztri_inverses(hm_handle_s *h, const C *T, int ldt, int n, C *Li, C *Ui)
+{
+    const size_t nn = (size_t)n * n;
+    k_eye<C><<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Li, n);
+    HM_CHECK_LAUNCH();
+    k_eye<C><<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Ui, n);
+    HM_CHECK_LAUNCH();
+    count_launch(h, 2);
+    for (int b0 = 0; b0 < n; b0 += TRS_BLK) {
+        const int nb = std::min(TRS_BLK, n - b0), b1 = b0 + nb, rest = n - b1;
+        trsm_left(h, 0, T + b0 + (size_t)b0 * ldt, ldt, nb, MVT<C>{Li + b0, nb, b1, n});
+        if (rest > 0)
+            zgemm<C>(h, 'N', 'N', rest, b1, nb, cmk<C>(-1, 0), T + b1 + (size_t)b0 * ldt, ldt, Li + b0, n,
+                     cmk<C>(1, 0), Li + b1, n);
+    }
+    for (int b1 = n; b1 > 0; b1 -= TRS_BLK) {
+        const int b0 = std::max(0, b1 - TRS_BLK), nb = b1 - b0;
+        trsm_left(h, 1, T + b0 + (size_t)b0 * ldt, ldt, nb, MVT<C>{Ui + b0 + (size_t)b0 * n, nb, n - b0, n});
+        if (b0 > 0)
+            zgemm<C>(h, 'N', 'N', b0, n - b0, nb, cmk<C>(-1, 0), T + (size_t)b0 * ldt, ldt, Ui + b0 + (size_t)b0 * n,
+                     n, cmk<C>(1, 0), Ui + (size_t)b0 * n, n);
+    }
+}
+
 // X = X U^-1 (X rows x n): one thread per row, sequential over columns.
 template <class C>
 __global__ void k_trsm_right_upper(const C *__restrict__ U, int ldu, int n, C *X, int ldx, int rows)
@@ -1810,6 +1840,7 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
     template void ztrsm_lun<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
     template void ztrsm_luh<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
     template void ztrsm_run<C>(hm_handle_s *, const C *, int, int, MVT<C>);                                       \
+    template void ztri_inverses<C>(hm_handle_s *, const C *, int, int, C *, C *);                                 \
     template void zcopy2d<C>(hm_handle_s *, MVT<C>, MVT<C>);                                                      \
     template void zscale_cols<C>(hm_handle_s *, MVT<C>, const typename CReal<C>::R *);                            \
     template int truncate_lr<C>(hm_handle_s *, int, int, int, const C *, int, const C *, int, double, int, C **, C **); \

@@ -354,6 +354,68 @@ static void make_map(CUtensorMap *map, const void *ptr, int rows, int kp, int bo
     if (r != CUDA_SUCCESS) throw HmError{HM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
 }
 
+static void launch_tc(int st, dim3 grid, cudaStream_t stream, const CUtensorMap &ma, const CUtensorMap &mb, int m,
+                      int n, int kp, cf alpha, cf beta, cf *Cm, int ldc, int *err)
+{
+    if (st == 2)
+        k_tc_gemm<2><<<grid, TC_T, tc_smem<2>(), stream>>>(ma, mb, m, n, kp, alpha, beta, Cm, ldc, err);
+    else
+        k_tc_gemm<4><<<grid, TC_T, tc_smem<4>(), stream>>>(ma, mb, m, n, kp, alpha, beta, Cm, ldc, err);
+    HM_CHECK_LAUNCH();
+}
+
+// Stage-count autotuner.  Per depth class (kp = 64 .. 4096 by powers of two) the first
+// product with at least 2 x 4096 x 4096 outputs' worth of work times both pipeline variants
+// (4 stages, one CTA per SM; 2 stages, two CTAs per SM) on its leading 4096 x 4096 block
+// into a scratch output, three launches each, and keeps the faster for every later product
+// of that class.  Until a class is tuned: 2 stages for kp <= 512, else 4.
+static int g_tc_stages[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+static float g_tc_tune_ms[8][2];
+
+static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &mb, int m, int n, int kp, int *err)
+{
+    int cls = 0;
+    while ((TC_BK << cls) < kp && cls < 7) ++cls;
+    if (g_tc_stages[cls]) return g_tc_stages[cls];
+    const int dflt = kp <= 512 ? 2 : 4;
+    if (m < 2048 || n < 2048) return dflt;
+    const int ms = std::min(m, 4096), ns = std::min(n, 4096);
+    cf *scratch = (cf *)dalloc(h, sizeof(cf) * (size_t)ms * ns);
+    const dim3 grid((2 * ms + TC_BM - 1) / TC_BM, (2 * ns + TC_BN - 1) / TC_BN);
+    cudaEvent_t e0 = gemm_event(h), e1 = gemm_event(h);
+    float best[2] = {1e30f, 1e30f};
+    const int sts[2] = {2, 4};
+    for (int rep = 0; rep < 3; ++rep)
+        for (int v = 0; v < 2; ++v) {
+            HM_CUDA(cudaEventRecord(e0, h->stream));
+            launch_tc(sts[v], grid, h->stream, ma, mb, ms, ns, kp, cmk<cf>(1, 0), cmk<cf>(0, 0), scratch, ms, err);
+            HM_CUDA(cudaEventRecord(e1, h->stream));
+            HM_CUDA(cudaEventSynchronize(e1));
+            float t = 0;
+            HM_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            best[v] = std::min(best[v], t);
+        }
+    count_launch(h, 6);
+    h->gemm_free.push_back(e0);
+    h->gemm_free.push_back(e1);
+    dfree(h, scratch);
+    g_tc_tune_ms[cls][0] = best[0];
+    g_tc_tune_ms[cls][1] = best[1];
+    g_tc_stages[cls] = best[0] <= best[1] ? 2 : 4;
+    return g_tc_stages[cls];
+}
+
+// The autotuner's record: per depth class kp = 64 << c (c = 0..7) the chosen stage count
+// (0: not tuned) and the two measured times (ms).
+void tc_tune_record(int *stages, float *ms2)
+{
+    for (int c = 0; c < 8; ++c) {
+        stages[c] = g_tc_stages[c];
+        ms2[2 * c] = g_tc_tune_ms[c][0];
+        ms2[2 * c + 1] = g_tc_tune_ms[c][1];
+    }
+}
+
 bool tc_eligible(const hm_handle_s *h, int m, int n, int k)
 {
     if (h->prm.simt_gemm) return false;
@@ -419,13 +481,10 @@ void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, 
         if (timed) {
             e0 = gemm_event(h);
             e1 = gemm_event(h);
-            HM_CUDA(cudaEventRecord(e0, h->stream));
         }
-        if (kp <= 512)
-            k_tc_gemm<2><<<grid, TC_T, tc_smem<2>(), h->stream>>>(ma, mb, m, n, kp, alpha, bet, Cm, ldc, err);
-        else
-            k_tc_gemm<4><<<grid, TC_T, tc_smem<4>(), h->stream>>>(ma, mb, m, n, kp, alpha, bet, Cm, ldc, err);
-        HM_CHECK_LAUNCH();
+        const int st = tc_stages(h, ma, mb, m, n, kp, err);
+        if (timed) HM_CUDA(cudaEventRecord(e0, h->stream));  // after any tuning launches
+        launch_tc(st, grid, h->stream, ma, mb, m, n, kp, alpha, bet, Cm, ldc, err);
         if (timed) {
             HM_CUDA(cudaEventRecord(e1, h->stream));
             h->gemm_pending.push_back(GemmTiming{e0, e1, fl, 1});

@@ -269,22 +269,6 @@ __global__ void __launch_bounds__(TL_T) k_tile_mul(int r0, int rows, int nrhs, c
     }
 }
 
-template <class C>
-__global__ void k_tile_identity(C *I, int n)
-{
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < (size_t)n * n) I[idx] = cmk<C>((idx % n) == (idx / n) ? 1 : 0, 0);
-}
-
-template <class C>
-static void identity_fill(hm_handle_s *h, C *I, int n)
-{
-    size_t nn = (size_t)n * n;
-    k_tile_identity<C><<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(I, n);
-    HM_CHECK_LAUNCH();
-    count_launch(h);
-}
-
 // Dynamic shared memory of k_tile_partial (the accumulators of one tile); raises the
 // kernel's limit when a tile needs more than the default 48 KB.
 template <class C>
@@ -566,10 +550,7 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                 const size_t o = (size_t)(T->r0[i] - d->r0);
                 const C *Dii = d->D + o + o * d->nr;
                 C *Li = T->d_inv + T->inv_off[i], *Ui = Li + (size_t)n * n;
-                identity_fill(h, Li, n);
-                identity_fill(h, Ui, n);
-                ztrsm_lln(h, Dii, d->nr, n, MVT<C>{Li, n, n, n});
-                ztrsm_lun(h, Dii, d->nr, n, MVT<C>{Ui, n, n, n});
+                ztri_inverses(h, Dii, d->nr, n, Li, Ui);
             }
             // the pivots of each diagonal leaf as one gather: applying the interchanges
             // k <-> piv[k] in order to z is z_new[j] = z_old[g[j]]

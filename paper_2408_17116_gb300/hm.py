@@ -36,7 +36,7 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
            "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host",
-           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host", "hm_cgemm")
+           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host", "hm_cgemm", "hm_tc_tuning")
 
 
 class hm_params(ctypes.Structure):
@@ -90,6 +90,7 @@ def load(path=SO):
     L.hm_muller_rhs_farfield_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, P, P, P, P, I, P, P]
     L.hm_query.argtypes = [P, I, ctypes.POINTER(D)]
     L.hm_inject_fault.argtypes = [P, I]
+    L.hm_tc_tuning.argtypes = [P, P]
     L.hm_cgemm.argtypes = [P, ctypes.c_char, ctypes.c_char, I, I, I, P, P, I, P, I, P, P, I, I]
     L.hm_get_trunc_log_host.argtypes = [P, ctypes.POINTER(I), P]
     L.hm_destroy.argtypes = [P]
@@ -207,6 +208,16 @@ def make_bodies(bodies, ms):
         for d in range(9):
             arr[i].rot[d] = b[6 + d]
     return arr
+
+
+def tc_tuning():
+    """The tensor-core autotuner's record: (stages[8], ms[8, 2]) per depth class 64 << c."""
+    st = np.zeros(8, dtype=np.int32)
+    ms = np.zeros(16, dtype=np.float32)
+    r = load().hm_tc_tuning(_np_ptr(st), _np_ptr(ms))
+    if r != HM_OK:
+        raise HmError(r, "hm_tc_tuning")
+    return st, ms.reshape(8, 2)
 
 
 class Solver:

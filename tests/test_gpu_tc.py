@@ -102,3 +102,24 @@ def test_tensor_core_path_rejects_small_shapes():
         s.hm_cgemm("N", "N", 1.0, A, A, 0.0, C, path=2)
     assert e.value.status == ARG
     s.close()
+
+
+def test_stage_autotuner_keeps_the_faster_variant():
+    # the first large product of a depth class times both pipeline variants and keeps the
+    # faster one; the product itself is still exact to the split-BF16 bound
+    rng = np.random.default_rng(11)
+    m = n = 3000
+    k = 256
+    A, B, C0 = rand(rng, m, k), rand(rng, k, n), rand(rng, m, n)
+    s = hm.Solver()
+    C = colmajor(C0)
+    s.hm_cgemm("N", "N", -1.0, colmajor(A), colmajor(B), 1.0, C, path=2)
+    st, ms = hm.tc_tuning()
+    c = 2  # packed depth 256 = 64 << 2
+    assert st[c] in (2, 4), st
+    assert np.all(ms[c] > 0), ms
+    assert ms[c][0 if st[c] == 2 else 1] <= ms[c][1 if st[c] == 2 else 0]
+    ref = C0.astype(np.complex128) - A.astype(np.complex128) @ B.astype(np.complex128)
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64) + np.abs(C0)
+    assert np.max(np.abs(C.cpu().numpy() - ref) / scale) <= 3 * 2.0 ** -16 + (2 * k + 4) * 2.0 ** -24
+    s.close()
