@@ -277,17 +277,19 @@ hm_status hm_get_trunc_log_host(hm_handle h, int *nbatches, double *out);
  * m x k, op(B) k x n.  alpha and beta point at two floats (real, imaginary) on the host.
  * path 0: the dispatch hm_factor uses (tensor cores for products of at least 2e8 real
  * flops with m, n >= 64 and k >= 16, unless simt_gemm was set); 1: CUDA cores; 2: tensor
- * cores (HM_ERR_ARG when m or n < 64 or k < 16).  Runs on the handle's stream and
+ * cores, autotuned kernel variant; 3, 4, 5: tensor cores with the 2-stage, 4-stage or
+ * persistent variant (HM_ERR_ARG for 2..5 when m or n < 64 or k < 16).  Runs on the handle's stream and
  * synchronises it; HM_ERR_TIMEOUT when a bounded pipeline wait of the tensor-core kernel
  * expired (C is then unspecified).  Any handle state. */
 hm_status hm_cgemm(hm_handle h, char opA, char opB, int m, int n, int k, const float *alpha, const void *A, int lda,
                    const void *B, int ldb, const float *beta, void *C, int ldc, int path);
 
-/* The stage-count autotuner of the tensor-core products (process-wide): for each depth class
- * c = 0..7 (packed depth 64 << c), stages[c] = the pipeline depth chosen (2: two CTAs per SM,
- * 4: one CTA per SM; 0: not tuned yet) and ms[2c], ms[2c + 1] the best of three timed
- * launches of the 2- and the 4-stage variant on the class's first large product (a leading
- * block of at most 4096 x 4096 complex outputs, into scratch memory).  No GPU work. */
+/* The kernel-variant autotuner of the tensor-core products (process-wide): for each depth
+ * class c = 0..7 (packed depth 64 << c), stages[c] = the variant chosen (2: 2-stage ring, two
+ * CTAs per SM; 4: 4-stage ring, one CTA per SM; 1: persistent, double-buffered accumulators;
+ * 0: not tuned yet) and ms[3c .. 3c + 2] the best of three timed launches of the 2-stage,
+ * 4-stage and persistent variants on the class's first large product (a leading block of at
+ * most 4096 x 4096 complex outputs, into scratch memory).  No GPU work. */
 hm_status hm_tc_tuning(int *stages, float *ms);
 
 /* Host-side fault injection for tests of the error paths (the paper has no counterpart).

@@ -1043,18 +1043,20 @@ hm_status hm_cgemm(hm_handle h, char opA, char opB, int m, int n, int k, const f
     return guard(h, [&] {
         if ((opA != 'N' && opA != 'C') || (opB != 'N' && opB != 'C') || !alpha || !beta)
             throw HmError{HM_ERR_ARG, "hm_cgemm: op must be 'N' or 'C'; alpha, beta non-null"};
-        if (m < 0 || n < 0 || k < 0 || path < 0 || path > 2) throw HmError{HM_ERR_ARG, "hm_cgemm: bad size or path"};
+        if (m < 0 || n < 0 || k < 0 || path < 0 || path > 5) throw HmError{HM_ERR_ARG, "hm_cgemm: bad size or path"};
         if (m == 0 || n == 0) return;
         const int rowsA = opA == 'N' ? m : k, rowsB = opB == 'N' ? k : n;
         if (!C || ldc < std::max(1, m) || (k > 0 && (!A || !B || lda < std::max(1, rowsA) || ldb < std::max(1, rowsB))))
             throw HmError{HM_ERR_ARG, "hm_cgemm: null pointer or leading dimension too small"};
-        if (path == 2 && (m < 64 || n < 64 || k < 16))
+        if (path >= 2 && (m < 64 || n < 64 || k < 16))
             throw HmError{HM_ERR_ARG, "hm_cgemm: the tensor-core path needs m, n >= 64 and k >= 16"};
         const cf al = cmk<cf>(alpha[0], alpha[1]), be = cmk<cf>(beta[0], beta[1]);
         const int saved = h->prm.simt_gemm;
         try {
-            if (path == 2) {
-                tc_gemm(h, opA, opB, m, n, k, al, (const cf *)A, lda, (const cf *)B, ldb, be, (cf *)C, ldc);
+            if (path >= 2) {
+                static const int variant[4] = {0, 2, 4, 1};  // path 2: autotuned; 3, 4, 5: forced
+                tc_gemm(h, opA, opB, m, n, k, al, (const cf *)A, lda, (const cf *)B, ldb, be, (cf *)C, ldc,
+                        variant[path - 2]);
             } else {
                 if (path == 1) h->prm.simt_gemm = 1;
                 zgemm<cf>(h, opA, opB, m, n, k, al, (const cf *)A, lda, (const cf *)B, ldb, be, (cf *)C, ldc);

@@ -294,10 +294,11 @@ struct PhaseScope {
 
 // ---- hm_tc.cu (complex64 GEMM on the tensor cores, split-BF16) ----
 bool tc_eligible(const hm_handle_s *h, int m, int n, int k);
+// variant: 0 = autotuned, 2 / 4 = 2- / 4-stage ring, 1 = persistent
 void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, const cf *A, int lda, const cf *B,
-             int ldb, cf beta, cf *Cm, int ldc);
+             int ldb, cf beta, cf *Cm, int ldc, int variant = 0);
 void tc_check(hm_handle_s *h);  // after a synchronisation: HM_ERR_TIMEOUT if a pipeline wait expired
-void tc_tune_record(int *stages, float *ms2);  // the stage-count autotuner's choices and timings
+void tc_tune_record(int *stages, float *ms3);  // the variant autotuner's choices and timings
 
 // ---- hm_io.cu ----
 void launch_rhs(hm_handle_s *h, int nrhs, const double *d_dirs, zc *d_b);  // tree order

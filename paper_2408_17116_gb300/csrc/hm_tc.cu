@@ -191,6 +191,49 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Epilogue of one warp: accumulator lanes of real rows R (this lane) of a 128 x 256 tile whose
+// TMEM lane quarter starts at taddr; C = alpha P + beta C for the tile's complex columns from
+// n0 / 2.  Warp-collective (tcgen05.ld): all 32 lanes, converged.
+__device__ __forceinline__ void tc_store_rows(uint32_t taddr, int R, int m, int n, int n0, float2 alpha, float2 beta,
+                                              float2 *__restrict__ Cm, int ldc)
+{
+    const int gi = R >> 1;  // complex row of C
+    const bool odd = threadIdx.x & 1;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(taddr + (uint32_t)c0, v);
+        // even lane (real part of op(A)): P_r* of complex columns q = 0..15 of this chunk;
+        // odd lane: P_i*.  The even lane finishes columns 0..7, the odd lane 8..15.
+        float mine[16], other[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float send = __uint_as_float(odd ? v[q] : v[16 + q]);
+            other[q] = __shfl_xor_sync(0xffffffffu, send, 1);
+            mine[q] = __uint_as_float(odd ? v[16 + q] : v[q]);
+        }
+        const int jb = (n0 + c0) / 2 + (odd ? 8 : 0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float prr = odd ? other[2 * q] : mine[2 * q];
+            const float pri = odd ? other[2 * q + 1] : mine[2 * q + 1];
+            const float pir = odd ? mine[2 * q] : other[2 * q];
+            const float pii = odd ? mine[2 * q + 1] : other[2 * q + 1];
+            const float cr = prr - pii, ci = pri + pir;
+            const int j = jb + q;
+            if (gi < m && j < n) {
+                float2 *cp = Cm + (size_t)j * ldc + gi;
+                float2 o = make_float2(alpha.x * cr - alpha.y * ci, alpha.x * ci + alpha.y * cr);
+                if (beta.x != 0.f || beta.y != 0.f) {
+                    const float2 c = *cp;
+                    o.x += beta.x * c.x - beta.y * c.y;
+                    o.y += beta.x * c.y + beta.y * c.x;
+                }
+                *cp = o;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // GEMM: C (m x n complex, ld ldc) = alpha P + beta C for the tile (blockIdx.x, blockIdx.y)
 // of P = Ar Br^T, with K = 3 kp (passes hi.hi, hi.lo, lo.hi over the packed operands).
@@ -275,44 +318,7 @@ __global__ void __launch_bounds__(TC_T, 1)
     const bool ok = __all_sync(0xffffffffu, mine_ok && *(volatile int *)err == 0);
     __syncwarp();
     tc_fence_after();
-    if (ok) {
-        const int R = m0 + warp * 32 + lane;  // real row of Ar
-        const int gi = R >> 1;                // complex row of C
-        const bool odd = lane & 1;
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            // even lane (real part of op(A)): P_r* of complex columns q = 0..15 of this chunk;
-            // odd lane: P_i*.  The even lane finishes columns 0..7, the odd lane 8..15.
-            float mine[16], other[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float send = __uint_as_float(odd ? v[q] : v[16 + q]);
-                other[q] = __shfl_xor_sync(0xffffffffu, send, 1);
-                mine[q] = __uint_as_float(odd ? v[16 + q] : v[q]);
-            }
-            const int jb = (n0 + c0) / 2 + (odd ? 8 : 0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float prr = odd ? other[2 * q] : mine[2 * q];
-                const float pri = odd ? other[2 * q + 1] : mine[2 * q + 1];
-                const float pir = odd ? mine[2 * q] : other[2 * q];
-                const float pii = odd ? mine[2 * q + 1] : other[2 * q + 1];
-                const float cr = prr - pii, ci = pri + pir;
-                const int j = jb + q;
-                if (gi < m && j < n) {
-                    float2 *cp = Cm + (size_t)j * ldc + gi;
-                    float2 o = make_float2(alpha.x * cr - alpha.y * ci, alpha.x * ci + alpha.y * cr);
-                    if (beta.x != 0.f || beta.y != 0.f) {
-                        const float2 c = *cp;
-                        o.x += beta.x * c.x - beta.y * c.y;
-                        o.y += beta.x * c.y + beta.y * c.x;
-                    }
-                    *cp = o;
-                }
-            }
-        }
-    }
+    if (ok) tc_store_rows(tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32 + lane, m, n, n0, alpha, beta, Cm, ldc);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -320,6 +326,133 @@ __global__ void __launch_bounds__(TC_T, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
     }
 }
+
+// ---------------------------------------------------------------------------
+// Persistent variant: one CTA per SM walks the output tiles (tile c, c + G, c + 2G, ...),
+// with two TMEM accumulators (512 columns) so that the epilogue of one tile runs under the
+// main loop of the next.  Six warps: 0 TMA producer, 1 MMA issuer, 2-5 epilogue (TMEM lane
+// quarters 2, 3, 0, 1).  4-stage operand ring as above; accumulator hand-off through
+// tfull[b] (MMA -> epilogue, tcgen05.commit) and tempty[b] (epilogue -> MMA, 128 arrivals).
+// ---------------------------------------------------------------------------
+#define TCP_T 192
+#define TCP_ST 4
+
+__global__ void __launch_bounds__(TCP_T, 1)
+    k_tc_gemm_p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int kp,
+                int tiles_x, int ntiles, float2 alpha, float2 beta, float2 *__restrict__ Cm, int ldc, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    const uint32_t raw = smem_u32(tc_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = tc_raw + (base - raw);
+    const uint32_t sA = base, sB = base + TCP_ST * TC_A_BYTES;
+    const uint32_t bars = base + TCP_ST * TC_STAGE_BYTES;  // full[ST], empty[ST], tfull[2], tempty[2]
+    auto full = [&](int s) { return bars + 8u * s; };
+    auto empty = [&](int s) { return bars + 8u * (TCP_ST + s); };
+    auto tfull = [&](int b) { return bars + 8u * (2 * TCP_ST + b); };
+    auto tempty = [&](int b) { return bars + 8u * (2 * TCP_ST + 2 + b); };
+    uint32_t *tslot = (uint32_t *)(gbase + TCP_ST * TC_STAGE_BYTES + 8 * (2 * TCP_ST + 4));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TCP_ST; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1);
+            mbar_init(tempty(b), 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(2 * TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int KB = kp / TC_BK, KT = 3 * KB;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool alive = true;
+            for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+                const int m0 = (t % tiles_x) * TC_BM, n0 = (t / tiles_x) * TC_BN;
+                for (int it = 0; it < KT; ++it, ++g) {
+                    const int s = g % TCP_ST;
+                    if (!mbar_wait(empty(s), ((g / TCP_ST) & 1) ^ 1, err)) {
+                        alive = false;
+                        break;
+                    }
+                    const int pass = it / KB, kb = it - pass * KB;
+                    mbar_expect_tx(full(s), TC_STAGE_BYTES);
+                    tma_load_2d(sA + s * TC_A_BYTES, &tmA, (pass == 2 ? kp : 0) + kb * TC_BK, m0, full(s));
+                    tma_load_2d(sB + s * TC_B_BYTES, &tmB, (pass == 1 ? kp : 0) + kb * TC_BK, n0, full(s));
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc_idesc();
+            uint32_t g = 0;
+            bool alive = true;
+            int j = 0;
+            for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++j) {
+                const int ab = j & 1;
+                if (!mbar_wait(tempty(ab), ((j >> 1) & 1) ^ 1, err)) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(ab * TC_BN);
+                for (int it = 0; it < KT; ++it, ++g) {
+                    const int s = g % TCP_ST;
+                    if (!mbar_wait(full(s), (g / TCP_ST) & 1, err)) {
+                        alive = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = sdesc_sw128(sA + s * TC_A_BYTES), db = sdesc_sw128(sB + s * TC_B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk)
+                        tc_mma(acc, da + 2 * kk, db + 2 * kk, idesc, (it | kk) != 0 ? 1u : 0u);
+                    tc_commit(empty(s));
+                }
+                tc_commit(tfull(ab));
+            }
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;  // TMEM lane quarter of this warp
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int ab = j & 1;
+            const bool mine_ok = mbar_wait(tfull(ab), (j >> 1) & 1, err);
+            const bool ok = __all_sync(0xffffffffu, mine_ok && *(volatile int *)err == 0);
+            __syncwarp();
+            if (!ok) break;
+            tc_fence_after();
+            const int m0 = (t % tiles_x) * TC_BM, n0 = (t / tiles_x) * TC_BN;
+            tc_store_rows(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * TC_BN), m0 + q * 32 + lane, m, n, n0,
+                          alpha, beta, Cm, ldc);
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty(ab)) : "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+    }
+}
+
+constexpr int tcp_smem() { return TCP_ST * TC_STAGE_BYTES + 1024 + 256; }
 
 // ---------------------------------------------------------------------------
 // host side
@@ -354,23 +487,36 @@ static void make_map(CUtensorMap *map, const void *ptr, int rows, int kp, int bo
     if (r != CUDA_SUCCESS) throw HmError{HM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
 }
 
+// Variants: 2 = 2-stage ring, two CTAs per SM; 4 = 4-stage ring, one CTA per SM; 1 =
+// persistent (one CTA per SM over all tiles, double-buffered accumulators).
 static void launch_tc(int st, dim3 grid, cudaStream_t stream, const CUtensorMap &ma, const CUtensorMap &mb, int m,
                       int n, int kp, cf alpha, cf beta, cf *Cm, int ldc, int *err)
 {
-    if (st == 2)
+    if (st == 2) {
         k_tc_gemm<2><<<grid, TC_T, tc_smem<2>(), stream>>>(ma, mb, m, n, kp, alpha, beta, Cm, ldc, err);
-    else
+    } else if (st == 4) {
         k_tc_gemm<4><<<grid, TC_T, tc_smem<4>(), stream>>>(ma, mb, m, n, kp, alpha, beta, Cm, ldc, err);
+    } else {
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            HM_CUDA(cudaGetDevice(&dev));
+            HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        }
+        const int ntiles = (int)(grid.x * grid.y);
+        k_tc_gemm_p<<<std::min(ntiles, nsm), TCP_T, tcp_smem(), stream>>>(ma, mb, m, n, kp, (int)grid.x, ntiles, alpha,
+                                                                          beta, Cm, ldc, err);
+    }
     HM_CHECK_LAUNCH();
 }
 
-// Stage-count autotuner.  Per depth class (kp = 64 .. 4096 by powers of two) the first
-// product with at least 2 x 4096 x 4096 outputs' worth of work times both pipeline variants
-// (4 stages, one CTA per SM; 2 stages, two CTAs per SM) on its leading 4096 x 4096 block
-// into a scratch output, three launches each, and keeps the faster for every later product
-// of that class.  Until a class is tuned: 2 stages for kp <= 512, else 4.
+// Variant autotuner.  Per depth class (kp = 64 .. 4096 by powers of two) the first product
+// with m, n >= 2048 times the three kernel variants (2 stages, two CTAs per SM; 4 stages, one
+// CTA per SM; persistent with double-buffered accumulators) on its leading block of at most
+// 4096 x 4096 outputs into a scratch output, three launches each, and keeps the fastest for
+// every later product of that class.  Until a class is tuned: 2 stages for kp <= 512, else 4.
 static int g_tc_stages[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-static float g_tc_tune_ms[8][2];
+static float g_tc_tune_ms[8][3];
 
 static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &mb, int m, int n, int kp, int *err)
 {
@@ -383,10 +529,10 @@ static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &m
     cf *scratch = (cf *)dalloc(h, sizeof(cf) * (size_t)ms * ns);
     const dim3 grid((2 * ms + TC_BM - 1) / TC_BM, (2 * ns + TC_BN - 1) / TC_BN);
     cudaEvent_t e0 = gemm_event(h), e1 = gemm_event(h);
-    float best[2] = {1e30f, 1e30f};
-    const int sts[2] = {2, 4};
+    float best[3] = {1e30f, 1e30f, 1e30f};
+    const int sts[3] = {2, 4, 1};
     for (int rep = 0; rep < 3; ++rep)
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < 3; ++v) {
             HM_CUDA(cudaEventRecord(e0, h->stream));
             launch_tc(sts[v], grid, h->stream, ma, mb, ms, ns, kp, cmk<cf>(1, 0), cmk<cf>(0, 0), scratch, ms, err);
             HM_CUDA(cudaEventRecord(e1, h->stream));
@@ -395,24 +541,26 @@ static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &m
             HM_CUDA(cudaEventElapsedTime(&t, e0, e1));
             best[v] = std::min(best[v], t);
         }
-    count_launch(h, 6);
+    count_launch(h, 9);
     h->gemm_free.push_back(e0);
     h->gemm_free.push_back(e1);
     dfree(h, scratch);
-    g_tc_tune_ms[cls][0] = best[0];
-    g_tc_tune_ms[cls][1] = best[1];
-    g_tc_stages[cls] = best[0] <= best[1] ? 2 : 4;
+    int bv = 0;
+    for (int v = 0; v < 3; ++v) {
+        g_tc_tune_ms[cls][v] = best[v];
+        if (best[v] < best[bv]) bv = v;
+    }
+    g_tc_stages[cls] = sts[bv];
     return g_tc_stages[cls];
 }
 
-// The autotuner's record: per depth class kp = 64 << c (c = 0..7) the chosen stage count
-// (0: not tuned) and the two measured times (ms).
-void tc_tune_record(int *stages, float *ms2)
+// The autotuner's record: per depth class kp = 64 << c (c = 0..7) the chosen variant
+// (2, 4 or 1 = persistent; 0: not tuned) and the three measured times (ms).
+void tc_tune_record(int *stages, float *ms3)
 {
     for (int c = 0; c < 8; ++c) {
         stages[c] = g_tc_stages[c];
-        ms2[2 * c] = g_tc_tune_ms[c][0];
-        ms2[2 * c + 1] = g_tc_tune_ms[c][1];
+        for (int v = 0; v < 3; ++v) ms3[3 * c + v] = g_tc_tune_ms[c][v];
     }
 }
 
@@ -432,13 +580,14 @@ int *tc_err_flag(hm_handle_s *h)
 }
 
 void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, const cf *A, int lda, const cf *B,
-             int ldb, cf beta, cf *Cm, int ldc)
+             int ldb, cf beta, cf *Cm, int ldc, int variant)
 {
     if (m <= 0 || n <= 0 || k <= 0) throw HmError{HM_ERR_ARG, "tc_gemm: empty product"};
     static bool attr = false;
     if (!attr) {
         HM_CUDA(cudaFuncSetAttribute(k_tc_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<4>()));
         HM_CUDA(cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<2>()));
+        HM_CUDA(cudaFuncSetAttribute(k_tc_gemm_p, cudaFuncAttributeMaxDynamicSharedMemorySize, tcp_smem()));
         attr = true;
     }
     int *err = tc_err_flag(h);
@@ -482,7 +631,7 @@ void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, 
             e0 = gemm_event(h);
             e1 = gemm_event(h);
         }
-        const int st = tc_stages(h, ma, mb, m, n, kp, err);
+        const int st = variant ? variant : tc_stages(h, ma, mb, m, n, kp, err);
         if (timed) HM_CUDA(cudaEventRecord(e0, h->stream));  // after any tuning launches
         launch_tc(st, grid, h->stream, ma, mb, m, n, kp, alpha, bet, Cm, ldc, err);
         if (timed) {

@@ -67,12 +67,24 @@ __device__ __forceinline__ void tile_gemv(const C *__restrict__ A, int ld, int r
 {
     const int tid = threadIdx.x;
     if (rows > TL_T) {
-        // tiles taller than the CTA: each thread owns rows tid, tid + TL_T, ...
+        // tiles taller than the CTA: each thread owns rows tid, tid + TL_T, ...; four columns
+        // per step, their loads issued together (memory-level parallelism)
         for (int r = tid; r < rows; r += TL_T) {
             C a[TL_NRB];
 #pragma unroll
             for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
-            for (int j = 0; j < n; ++j) {
+            int j = 0;
+            for (; j + 4 <= n; j += 4) {
+                C v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = A[(size_t)(j + u) * ld + r];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int c = 0; c < TL_NRB; ++c)
+                        if (c < nrb) a[c] = zfma(v[u], zs[(j + u) * TL_NRB + c], a[c]);
+            }
+            for (; j < n; ++j) {
                 C v = A[(size_t)j * ld + r];
 #pragma unroll
                 for (int c = 0; c < TL_NRB; ++c)
@@ -91,7 +103,18 @@ __device__ __forceinline__ void tile_gemv(const C *__restrict__ A, int ld, int r
 #pragma unroll
     for (int c = 0; c < TL_NRB; ++c) a[c] = cmk<C>(0, 0);
     if (g < G && tid < G * rows) {
-        for (int j = g; j < n; j += G) {
+        int j = g;
+        for (; j + 3 * G < n; j += 4 * G) {
+            C v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = A[(size_t)(j + u * G) * ld + r];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int c = 0; c < TL_NRB; ++c)
+                    if (c < nrb) a[c] = zfma(v[u], zs[(j + u * G) * TL_NRB + c], a[c]);
+        }
+        for (; j < n; j += G) {
             C v = A[(size_t)j * ld + r];
 #pragma unroll
             for (int c = 0; c < TL_NRB; ++c)
@@ -236,14 +259,20 @@ __global__ void k_tile_put(int r0, int rows, int nrhs, const C *__restrict__ z, 
     }
 }
 
-// Sweep step, part 2 (CTAs over blocks of TL_T rows): X[r0 + i, c] = sum_j Minv[i][j] z[j][c],
-// Minv the explicit inverse of the diagonal block's triangular factor (column-major).
+// Sweep step, part 2: X[r0 + i, c] = sum_j Minv[i][j] z[j][c], Minv the explicit inverse of
+// the diagonal block's triangular factor (column-major).  A CTA owns 32 rows; its 8 warps
+// take every 8th column (lane = row, so each column's 32 entries load as one 256-byte
+// transaction) and their partial sums are added in warp order (deterministic).
+#define TM_R 32
+#define TM_G (TL_T / TM_R)
 template <class C>
 __global__ void __launch_bounds__(TL_T) k_tile_mul(int r0, int rows, int nrhs, const C *__restrict__ Minv,
                                                      const C *__restrict__ z, C *X, int ldx)
 {
     __shared__ C zs[TL_T * TL_NRB];
-    const int i = blockIdx.x * TL_T + threadIdx.x;
+    __shared__ C red[TM_G][TM_R][TL_NRB];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = blockIdx.x * TM_R + lane;
     for (int cb = 0; cb < nrhs; cb += TL_NRB) {
         const int nrb = min(TL_NRB, nrhs - cb);
         C a[TL_NRB];
@@ -257,15 +286,34 @@ __global__ void __launch_bounds__(TL_T) k_tile_mul(int r0, int rows, int nrhs, c
                 zs[e] = c < nrb ? z[(size_t)(cb + c) * rows + j0 + j] : cmk<C>(0, 0);
             }
             __syncthreads();
-            if (i < rows)
-                for (int j = 0; j < nj; ++j) {
-                    C m = Minv[(size_t)(j0 + j) * rows + i];
+            if (i < rows) {
+                int j = g;
+                for (; j + 3 * TM_G < nj; j += 4 * TM_G) {
+                    C mv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) mv[u] = Minv[(size_t)(j0 + j + u * TM_G) * rows + i];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int c = 0; c < TL_NRB; ++c) a[c] = zfma(mv[u], zs[(j + u * TM_G) * TL_NRB + c], a[c]);
+                }
+                for (; j < nj; j += TM_G) {
+                    const C m = Minv[(size_t)(j0 + j) * rows + i];
 #pragma unroll
                     for (int c = 0; c < TL_NRB; ++c) a[c] = zfma(m, zs[j * TL_NRB + c], a[c]);
                 }
+            }
         }
-        if (i < rows)
-            for (int c = 0; c < nrb; ++c) X[(size_t)(cb + c) * ldx + r0 + i] = a[c];
+#pragma unroll
+        for (int c = 0; c < TL_NRB; ++c) red[g][lane][c] = a[c];
+        __syncthreads();
+        if (g == 0 && i < rows)
+            for (int c = 0; c < nrb; ++c) {
+                C s = red[0][lane][c];
+                for (int q = 1; q < TM_G; ++q) s = zadd(s, red[q][lane][c]);
+                X[(size_t)(cb + c) * ldx + r0 + i] = s;
+            }
+        __syncthreads();
     }
 }
 
@@ -635,7 +683,7 @@ void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
         const int rows = T->rows[i];
         k_tile_prep<C><<<grid_of(rows), TL_T, 0, h->stream>>>(T->r0[i], rows, nch, part, nrhs, T->rmax, g, X, T->N, z);
         HM_CHECK_LAUNCH();
-        k_tile_mul<C><<<(rows + TL_T - 1) / TL_T, TL_T, 0, h->stream>>>(T->r0[i], rows, nrhs, Minv, z, X, T->N);
+        k_tile_mul<C><<<(rows + TM_R - 1) / TM_R, TL_T, 0, h->stream>>>(T->r0[i], rows, nrhs, Minv, z, X, T->N);
         HM_CHECK_LAUNCH();
         count_launch(h, 2);
     };

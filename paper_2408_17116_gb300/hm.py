@@ -211,13 +211,15 @@ def make_bodies(bodies, ms):
 
 
 def tc_tuning():
-    """The tensor-core autotuner's record: (stages[8], ms[8, 2]) per depth class 64 << c."""
+    """The tensor-core autotuner's record: (variant[8], ms[8, 3]) per depth class 64 << c;
+    variant 2 / 4 = 2- / 4-stage ring, 1 = persistent, 0 = not tuned; ms columns in that
+    order (2-stage, 4-stage, persistent)."""
     st = np.zeros(8, dtype=np.int32)
-    ms = np.zeros(16, dtype=np.float32)
+    ms = np.zeros(24, dtype=np.float32)
     r = load().hm_tc_tuning(_np_ptr(st), _np_ptr(ms))
     if r != HM_OK:
         raise HmError(r, "hm_tc_tuning")
-    return st, ms.reshape(8, 2)
+    return st, ms.reshape(8, 3)
 
 
 class Solver:

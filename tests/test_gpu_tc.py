@@ -43,7 +43,8 @@ def op(x, o):
     return x if o == "N" else x.conj().T
 
 
-CASES = [(64, 64, 16), (200, 300, 100), (333, 517, 77), (1000, 700, 2500), (128, 256, 64), (97, 1290, 300)]
+CASES = [(64, 64, 16), (200, 300, 100), (333, 517, 77), (1000, 700, 2500), (128, 256, 64), (97, 1290, 300),
+         (2100, 1500, 256)]
 
 
 @pytest.mark.parametrize("m,n,k", CASES)
@@ -59,7 +60,9 @@ def test_tensor_core_gemm_against_fp64_product(m, n, k, opA, opB):
     scale = abs(alpha) * (np.abs(Ad) @ np.abs(Bd)) + abs(beta) * np.abs(C0)
     s = hm.Solver()
     acc = (2 * k + 4) * 2.0 ** -24
-    for path, tol in ((2, 3 * 2.0 ** -16 + acc), (1, acc)):
+    tc = 3 * 2.0 ** -16 + acc
+    # 2: autotuned variant; 3, 4, 5: the 2-stage, 4-stage and persistent kernels; 1: CUDA cores
+    for path, tol in ((2, tc), (3, tc), (4, tc), (5, tc), (1, acc)):
         C = colmajor(C0)
         s.hm_cgemm(opA, opB, alpha, colmajor(A), colmajor(B), beta, C, path=path)
         got = C.cpu().numpy()
@@ -116,9 +119,9 @@ def test_stage_autotuner_keeps_the_faster_variant():
     s.hm_cgemm("N", "N", -1.0, colmajor(A), colmajor(B), 1.0, C, path=2)
     st, ms = hm.tc_tuning()
     c = 2  # packed depth 256 = 64 << 2
-    assert st[c] in (2, 4), st
+    assert st[c] in (1, 2, 4), st
     assert np.all(ms[c] > 0), ms
-    assert ms[c][0 if st[c] == 2 else 1] <= ms[c][1 if st[c] == 2 else 0]
+    assert ms[c][{2: 0, 4: 1, 1: 2}[int(st[c])]] <= ms[c].min()
     ref = C0.astype(np.complex128) - A.astype(np.complex128) @ B.astype(np.complex128)
     scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64) + np.abs(C0)
     assert np.max(np.abs(C.cpu().numpy() - ref) / scale) <= 3 * 2.0 ** -16 + (2 * k + 4) * 2.0 ** -24
