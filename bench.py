@@ -29,6 +29,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "fill+factor+solve unknowns/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) of one k_near launch per near patch pair, from the ncu capture of
+# the 4,800-unknown sphere (0.630 MB read + 62.312 MB written for 192 pairs; part of the
+# written near store was still in L2 when that kernel ended, so this is a lower bound)
+NEAR_DRAM_BYTES_PER_PAIR = (0.630272e6 + 62.311936e6) / 192
 
 
 def tensor_peak():
@@ -432,8 +436,11 @@ def main():
     cands = []
     if per["T_NEAR"] > 0:
         a = near_flops / per["T_NEAR"] / 1e12
+        npairs = s.hm_query("NEAR_PAIRS")
         cands.append({"kernel": "k_near (self/near CBIE quadrature, FP64)", "bound": "alu", "achieved": a,
-                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_PEAK_TFLOPS, "traffic": None,
+                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_PEAK_TFLOPS,
+                      "traffic": NEAR_DRAM_BYTES_PER_PAIR * npairs if wl.get("formulation") != "MULLER" else None,
+                      "traffic_source": "ncu capture of the 4,800-unknown sphere (192 near pairs), scaled by near pairs",
                       "launches_per_step": 1, "seconds_per_step": per["T_NEAR"],
                       "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"})
     fp32 = prec == "fp32r"
@@ -485,6 +492,12 @@ def main():
            "roofline": roof, "kernels": cands[1:]}
     if rank_info is not None:
         out["rank_model"] = dict(rank_info, aca_skipped=s.hm_query("ACA_SKIPPED"), aca_reruns=s.hm_query("ACA_RERUNS"))
+    # the tensor-core variant autotuner: per packed depth 64 << c the chosen kernel (2 / 4 =
+    # 2- / 4-stage ring, 1 = persistent) and the timed milliseconds of the three variants
+    st, tms = hm.tc_tuning()
+    out["tc_tuning"] = {str(64 << c): {"variant": int(st[c]), "ms_2stage_4stage_persistent": [round(float(x), 4)
+                                                                                                for x in tms[c]]}
+                        for c in range(8) if st[c]}
     if not args.no_compare:
         # FP32 H-LU + FP64 refinement against the plain FP64 H-LU on the same GPU, one timed
         # step each, with each solution's error against the stored dense-oracle solution

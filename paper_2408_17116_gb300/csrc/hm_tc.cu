@@ -192,14 +192,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 }
 
 // Epilogue of one warp: accumulator lanes of real rows R (this lane) of a 128 x 256 tile whose
-// TMEM lane quarter starts at taddr; C = alpha P + beta C for the tile's complex columns from
-// n0 / 2.  Warp-collective (tcgen05.ld): all 32 lanes, converged.
+// TMEM lane quarter starts at taddr, accumulator columns [cbeg, cend); C = alpha P + beta C
+// for the tile's complex columns from n0 / 2.  Warp-collective (tcgen05.ld): all 32 lanes,
+// converged.
 __device__ __forceinline__ void tc_store_rows(uint32_t taddr, int R, int m, int n, int n0, float2 alpha, float2 beta,
-                                              float2 *__restrict__ Cm, int ldc)
+                                              float2 *__restrict__ Cm, int ldc, int cbeg = 0, int cend = TC_BN)
 {
     const int gi = R >> 1;  // complex row of C
     const bool odd = threadIdx.x & 1;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+    for (int c0 = cbeg; c0 < cend; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(taddr + (uint32_t)c0, v);
         // even lane (real part of op(A)): P_r* of complex columns q = 0..15 of this chunk;
@@ -330,11 +331,12 @@ __global__ void __launch_bounds__(TC_T, 1)
 // ---------------------------------------------------------------------------
 // Persistent variant: one CTA per SM walks the output tiles (tile c, c + G, c + 2G, ...),
 // with two TMEM accumulators (512 columns) so that the epilogue of one tile runs under the
-// main loop of the next.  Six warps: 0 TMA producer, 1 MMA issuer, 2-5 epilogue (TMEM lane
-// quarters 2, 3, 0, 1).  4-stage operand ring as above; accumulator hand-off through
-// tfull[b] (MMA -> epilogue, tcgen05.commit) and tempty[b] (epilogue -> MMA, 128 arrivals).
+// main loop of the next.  Ten warps: 0 TMA producer, 1 MMA issuer, 2-9 epilogue (TMEM lane
+// quarter = warp mod 4, the first or second half of the 256 accumulator columns).  4-stage
+// operand ring as above; accumulator hand-off through tfull[b] (MMA -> epilogue,
+// tcgen05.commit) and tempty[b] (epilogue -> MMA, 256 arrivals).
 // ---------------------------------------------------------------------------
-#define TCP_T 192
+#define TCP_T 320
 #define TCP_ST 4
 
 __global__ void __launch_bounds__(TCP_T, 1)
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(TCP_T, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull(b), 1);
-            mbar_init(tempty(b), 128);
+            mbar_init(tempty(b), TCP_T - 64);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -428,7 +430,8 @@ __global__ void __launch_bounds__(TCP_T, 1)
         }
         __syncwarp();
     } else {
-        const int q = warp & 3;  // TMEM lane quarter of this warp
+        const int q = warp & 3;                // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;      // accumulator columns [128 half, 128 half + 128)
         int j = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
             const int ab = j & 1;
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(TCP_T, 1)
             tc_fence_after();
             const int m0 = (t % tiles_x) * TC_BM, n0 = (t / tiles_x) * TC_BN;
             tc_store_rows(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * TC_BN), m0 + q * 32 + lane, m, n, n0,
-                          alpha, beta, Cm, ldc);
+                          alpha, beta, Cm, ldc, half * (TC_BN / 2), (half + 1) * (TC_BN / 2));
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty(ab)) : "memory");
         }
@@ -513,8 +516,9 @@ static void launch_tc(int st, dim3 grid, cudaStream_t stream, const CUtensorMap 
 // Variant autotuner.  Per depth class (kp = 64 .. 4096 by powers of two) the first product
 // with m, n >= 2048 times the three kernel variants (2 stages, two CTAs per SM; 4 stages, one
 // CTA per SM; persistent with double-buffered accumulators) on its leading block of at most
-// 4096 x 4096 outputs into a scratch output, three launches each, and keeps the fastest for
-// every later product of that class.  Until a class is tuned: 2 stages for kp <= 512, else 4.
+// 2^28 outputs, accumulating (beta = 1, so the epilogue reads and writes as in the H-LU's
+// updates) into scratch memory, twice each, and keeps the fastest for every later product of
+// that class.  Until a class is tuned: 2 stages for kp <= 512, else 4.
 static int g_tc_stages[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 static float g_tc_tune_ms[8][3];
 
@@ -525,23 +529,24 @@ static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &m
     if (g_tc_stages[cls]) return g_tc_stages[cls];
     const int dflt = kp <= 512 ? 2 : 4;
     if (m < 2048 || n < 2048) return dflt;
-    const int ms = std::min(m, 4096), ns = std::min(n, 4096);
+    const int ms = m, ns = (int)std::min<long long>(n, std::max<long long>(256, (1LL << 28) / m));
     cf *scratch = (cf *)dalloc(h, sizeof(cf) * (size_t)ms * ns);
     const dim3 grid((2 * ms + TC_BM - 1) / TC_BM, (2 * ns + TC_BN - 1) / TC_BN);
     cudaEvent_t e0 = gemm_event(h), e1 = gemm_event(h);
     float best[3] = {1e30f, 1e30f, 1e30f};
     const int sts[3] = {2, 4, 1};
-    for (int rep = 0; rep < 3; ++rep)
+    HM_CUDA(cudaMemsetAsync(scratch, 0, sizeof(cf) * (size_t)ms * ns, h->stream));
+    for (int rep = 0; rep < 2; ++rep)
         for (int v = 0; v < 3; ++v) {
             HM_CUDA(cudaEventRecord(e0, h->stream));
-            launch_tc(sts[v], grid, h->stream, ma, mb, ms, ns, kp, cmk<cf>(1, 0), cmk<cf>(0, 0), scratch, ms, err);
+            launch_tc(sts[v], grid, h->stream, ma, mb, ms, ns, kp, cmk<cf>(1, 0), cmk<cf>(1, 0), scratch, ms, err);
             HM_CUDA(cudaEventRecord(e1, h->stream));
             HM_CUDA(cudaEventSynchronize(e1));
             float t = 0;
             HM_CUDA(cudaEventElapsedTime(&t, e0, e1));
             best[v] = std::min(best[v], t);
         }
-    count_launch(h, 9);
+    count_launch(h, 6);
     h->gemm_free.push_back(e0);
     h->gemm_free.push_back(e1);
     dfree(h, scratch);
