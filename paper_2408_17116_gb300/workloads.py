@@ -77,6 +77,10 @@ def workload(name):
         kh, pol = axial_incidence()
         return dict(name=name, bodies=body(semi=(0.5,) * 3)[None], ms=[2], nc=12, k=K0, leaf=96, eta=2.0,
                     aca_tol=1e-8, kdirs=kh, pols=pol, radius=0.5, formulation="MULLER", eps_r=80.0)
+    if name == "ellipsoid_d30_m16_nc8":  # electrically large PEC ellipsoid, 196,608 unknowns, 181 RHS
+        kh, pol = monostatic_sweep(181)
+        return dict(name=name, bodies=body(semi=(3.75, 7.5, 15.0))[None], ms=[16], nc=8, k=K0, leaf=256, eta=2.0,
+                    aca_tol=1e-5, kdirs=kh, pols=pol)
     if name == "batch_spheroids64":  # 64 independent PEC prolate spheroids, 16 incidences each
         bodies, ms = spheroid_batch(64, SEED + 3)
         kh, pol = incidence(16, SEED + 4)
@@ -88,6 +92,15 @@ def workload(name):
         return dict(name=name, bodies=bodies, ms=ms, nc=8, k=K0, leaf=64, eta=2.0, aca_tol=1e-7, kdirs=kh,
                     pols=pol, independent=True)
     raise KeyError(name)
+
+
+def monostatic_sweep(n):
+    """n plane waves arriving from theta = 0..180 deg in the phi = 0 plane (k-hat = -r-hat),
+    polarised along theta-hat: the incidences of a monostatic RCS sweep."""
+    th = np.linspace(0.0, np.pi, n)
+    kh = -np.stack([np.sin(th), np.zeros(n), np.cos(th)], 1)
+    pol = np.stack([np.cos(th), np.zeros(n), -np.sin(th)], 1)
+    return kh, pol
 
 
 def spheroid_batch(n, seed, major=None):
@@ -110,7 +123,7 @@ def spheroid_batch(n, seed, major=None):
 
 
 WORKLOADS = ("sphere_d1_m1_nc8", "sphere_d8_m4_nc10", "sphere_d4_m2_nc10", "sphere_d2_m2_nc6", "ellipsoid_small",
-             "dielectric_d1_eps80_m2_nc12", "batch_spheroids64", "batch_spheroids3")
+             "dielectric_d1_eps80_m2_nc12", "batch_spheroids64", "batch_spheroids3", "ellipsoid_d30_m16_nc8")
 
 
 def mlp_init(nin, nh, seed=SEED):
