@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "hm_internal.h"
 
@@ -522,10 +523,13 @@ static void launch_tc(int st, dim3 grid, cudaStream_t stream, const CUtensorMap 
 static int g_tc_stages[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 static float g_tc_tune_ms[8][3];
 
+static std::mutex g_tc_tune_mutex;  // handles on different host threads share the record
+
 static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &mb, int m, int n, int kp, int *err)
 {
     int cls = 0;
     while ((TC_BK << cls) < kp && cls < 7) ++cls;
+    std::lock_guard<std::mutex> lock(g_tc_tune_mutex);
     if (g_tc_stages[cls]) return g_tc_stages[cls];
     const int dflt = kp <= 512 ? 2 : 4;
     if (m < 2048 || n < 2048) return dflt;
@@ -563,6 +567,7 @@ static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &m
 // (2, 4 or 1 = persistent; 0: not tuned) and the three measured times (ms).
 void tc_tune_record(int *stages, float *ms3)
 {
+    std::lock_guard<std::mutex> lock(g_tc_tune_mutex);
     for (int c = 0; c < 8; ++c) {
         stages[c] = g_tc_stages[c];
         for (int v = 0; v < 3; ++v) ms3[3 * c + v] = g_tc_tune_ms[c][v];

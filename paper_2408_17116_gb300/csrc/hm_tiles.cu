@@ -50,6 +50,8 @@ struct TPiece {
     int ld;         // leading dimension of A
     int c0, ncol;   // columns of the leaf (tree order)
     int k;          // rank (low-rank), 0 for dense
+    int toff;       // product plan: first rank column of the leaf's V^H X in the per-call buffer
+                    // (computed once per leaf by k_leaf_vhx); -1: the CTA forms V^H X itself
 };
 
 struct TChunk {
@@ -136,7 +138,8 @@ __device__ __forceinline__ void tile_gemv(const C *__restrict__ A, int ld, int r
 template <class C>
 __global__ void __launch_bounds__(TL_T) k_tile_partial(const TPiece<C> *__restrict__ pieces,
                                                          const TChunk *__restrict__ chunks, const C *__restrict__ X,
-                                                         int ldx, int nrhs, C *__restrict__ part, int rmax)
+                                                         int ldx, int nrhs, C *__restrict__ part, int rmax,
+                                                         const C *__restrict__ tbuf)
 {
     extern __shared__ __align__(16) unsigned char tp_raw[];
     C *acc = (C *)tp_raw;  // [rmax][TL_NRB]
@@ -163,6 +166,16 @@ __global__ void __launch_bounds__(TL_T) k_tile_partial(const TPiece<C> *__restri
             } else {
                 for (int k0 = 0; k0 < P.k; k0 += TL_KC) {
                     const int kc = min(TL_KC, P.k - k0);
+                    if (P.toff >= 0) {
+                        // V^H X of this leaf, formed once for all its row tiles
+                        for (int e = tid; e < kc * TL_NRB; e += TL_T) {
+                            const int kk = e / TL_NRB, c = e - kk * TL_NRB;
+                            zs[e] = c < nrb ? tbuf[(size_t)(P.toff + k0 + kk) * nrhs + cb + c] : cmk<C>(0, 0);
+                        }
+                        __syncthreads();
+                        tile_gemv<C, false>(P.A + (size_t)k0 * P.ld, P.ld, rows, kc, zs, nrb, acc);
+                        continue;
+                    }
                     // t[kk][c] = sum_j conj(V[j, k0 + kk]) X[c0 + j, cb + c]: one warp per column kk
                     for (int kk = warp; kk < kc; kk += TL_T / 32) {
                         const C *v = P.V + (size_t)(k0 + kk) * P.ncol;
@@ -198,6 +211,44 @@ __global__ void __launch_bounds__(TL_T) k_tile_partial(const TPiece<C> *__restri
             out[(size_t)(cb + c) * rmax + r] = acc[r * TL_NRB + c];
         }
         __syncthreads();
+    }
+}
+
+// V^H X of every low-rank leaf of a product plan, once per leaf: one warp per (leaf, rank
+// column) job; t[(toff + kk) nrhs + c] = sum_j conj(V[j, kk]) X[c0 + j, c].
+struct TLeaf {
+    int c0, ncol, toff;
+};
+template <class C>
+__global__ void __launch_bounds__(TL_T) k_leaf_vhx(const TLeaf *__restrict__ leaves, const int2 *__restrict__ jobs,
+                                                     const C *const *__restrict__ vptr, int njobs,
+                                                     const C *__restrict__ X, int ldx, int nrhs, C *__restrict__ t)
+{
+    const int lane = threadIdx.x & 31;
+    const int job = blockIdx.x * (TL_T / 32) + (threadIdx.x >> 5);
+    if (job >= njobs) return;
+    const int2 jb = jobs[job];
+    const TLeaf L = leaves[jb.x];
+    const C *v = vptr[jb.x] + (size_t)jb.y * L.ncol;
+    for (int cb = 0; cb < nrhs; cb += TL_NRB) {
+        const int nrb = min(TL_NRB, nrhs - cb);
+        C s[TL_NRB];
+#pragma unroll
+        for (int c = 0; c < TL_NRB; ++c) s[c] = cmk<C>(0, 0);
+        for (int j = lane; j < L.ncol; j += 32) {
+            const C vv = v[j];
+#pragma unroll
+            for (int c = 0; c < TL_NRB; ++c)
+                if (c < nrb) s[c] = zfmac(vv, X[(size_t)(cb + c) * ldx + L.c0 + j], s[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < TL_NRB; ++c)
+            for (int o = 16; o > 0; o >>= 1) {
+                s[c].x += __shfl_down_sync(0xffffffffu, s[c].x, o);
+                s[c].y += __shfl_down_sync(0xffffffffu, s[c].y, o);
+            }
+        if (lane == 0)
+            for (int c = 0; c < nrb; ++c) t[(size_t)(L.toff + jb.y) * nrhs + cb + c] = s[c];
     }
 }
 
@@ -354,6 +405,11 @@ struct TileOp {
     TChunk *d_co = nullptr;
     std::vector<int> co0, co1;
     int maxgrow = 0;                      // rows of the largest group
+    // product plan: V^H X once per low-rank leaf
+    TLeaf *d_tl = nullptr;
+    int2 *d_tjobs = nullptr;
+    const C **d_tv = nullptr;
+    int ntjobs = 0;                       // = total rank of the low-rank leaves
     std::vector<void *> owned;
 };
 
@@ -469,8 +525,18 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
         // pieces per tile: all / left of the diagonal (outside the tile's own diagonal leaf, and
         // inside it for a group) / right of the diagonal
         std::vector<std::vector<TPiece<C>>> all(T->ntile), left(T->ntile), lin(T->ntile), right(T->ntile);
+        std::vector<TLeaf> tl;
+        std::vector<int2> tjobs;
+        std::vector<const C *> tv;
         for (BlockT<C> *b : leaves) {
             if (b->type == B_LR && b->k == 0) continue;
+            int toff = -1;
+            if (b->type == B_LR) {
+                toff = (int)tjobs.size();
+                for (int kk = 0; kk < b->k; ++kk) tjobs.push_back(make_int2((int)tl.size(), kk));
+                tl.push_back(TLeaf{b->c0, b->nc, toff});
+                tv.push_back(b->V);
+            }
             const bool isdiag = b->r0 == b->c0 && b->type == B_DENSE && b->nr == b->nc;
             for (int i = tile_of(b->r0); i < T->ntile && T->r0[i] < b->r0 + b->nr; ++i) {
                 if (T->r0[i] < b->r0 || T->r0[i] + T->rows[i] > b->r0 + b->nr)
@@ -480,6 +546,7 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                 p.ld = b->nr;
                 p.c0 = b->c0;
                 p.ncol = b->nc;
+                p.toff = -1;
                 if (b->type == B_DENSE) {
                     p.A = b->D + rofs;
                     p.V = nullptr;
@@ -489,7 +556,11 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                     p.V = b->V;
                     p.k = b->k;
                 }
-                push_piece(all[i], p, T->rows[i]);
+                {
+                    TPiece<C> pa = p;
+                    pa.toff = toff;  // the product plan reads V^H X from the per-call buffer
+                    push_piece(all[i], pa, T->rows[i]);
+                }
                 if (isdiag) {
                     // a grouped diagonal leaf: its off-diagonal tile blocks L_ij (j < i), U_ij (j > i)
                     for (int j = T->grp0[i]; j < T->grp0[i] + T->grpn[i]; ++j) {
@@ -501,6 +572,7 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                         q.c0 = T->r0[j];
                         q.ncol = T->rows[j];
                         q.k = 0;
+                        q.toff = -1;
                         push_piece(j < i ? lin[i] : right[i], q, T->rows[i]);
                     }
                     continue;
@@ -531,6 +603,10 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
                 s1[i] = slot;
             }
             T->nca = (int)chs.size();
+            T->ntjobs = (int)tjobs.size();
+            T->d_tl = upload(h, tl, T->owned);
+            T->d_tjobs = upload(h, tjobs, T->owned);
+            T->d_tv = upload(h, tv, T->owned);
             T->d_pa = upload(h, pcs, T->owned);
             T->d_ca = upload(h, chs, T->owned);
             T->d_tr0 = upload(h, T->r0, T->owned);
@@ -650,9 +726,17 @@ void tile_matvec(hm_handle_s *h, TileOp<C> *T, const C *X, C *Y, int nrhs, C alp
 {
     if (nrhs <= 0 || T->ntile == 0) return;
     C *part = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->nca, 1) * nrhs * T->rmax);
+    C *tbuf = (C *)dalloc(h, sizeof(C) * (size_t)std::max(T->ntjobs, 1) * nrhs);
     const size_t smem = partial_smem<C>(T->rmax);
+    if (T->ntjobs) {
+        const int per = TL_T / 32;
+        k_leaf_vhx<C><<<(T->ntjobs + per - 1) / per, TL_T, 0, h->stream>>>(T->d_tl, T->d_tjobs, T->d_tv, T->ntjobs, X,
+                                                                           T->N, nrhs, tbuf);
+        HM_CHECK_LAUNCH();
+        count_launch(h);
+    }
     if (T->nca) {
-        k_tile_partial<C><<<T->nca, TL_T, smem, h->stream>>>(T->d_pa, T->d_ca, X, T->N, nrhs, part, T->rmax);
+        k_tile_partial<C><<<T->nca, TL_T, smem, h->stream>>>(T->d_pa, T->d_ca, X, T->N, nrhs, part, T->rmax, tbuf);
         HM_CHECK_LAUNCH();
     }
     k_tile_reduce<C><<<T->ntile, TL_T, 0, h->stream>>>(T->d_tr0, T->d_trows, T->d_ts0, T->d_ts1, part, nrhs,
@@ -660,6 +744,7 @@ void tile_matvec(hm_handle_s *h, TileOp<C> *T, const C *X, C *Y, int nrhs, C alp
     HM_CHECK_LAUNCH();
     count_launch(h, T->nca ? 2 : 1);
     dfree(h, part);
+    dfree(h, tbuf);
 }
 
 // X <- A^-1 X with the H-LU factors (tree order, N x nrhs, ld N).
@@ -674,7 +759,7 @@ void tile_solve(hm_handle_s *h, TileOp<C> *T, C *X, int nrhs)
     auto grid_of = [&](int rows) { return std::max(1, std::min(64, (int)((rows * (size_t)nrhs + TL_T - 1) / TL_T))); };
     auto partial = [&](const TPiece<C> *pcs, const TChunk *chs, int nch) {
         if (!nch) return;
-        k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(pcs, chs, X, T->N, nrhs, part, T->rmax);
+        k_tile_partial<C><<<nch, TL_T, psmem, h->stream>>>(pcs, chs, X, T->N, nrhs, part, T->rmax, nullptr);
         HM_CHECK_LAUNCH();
         count_launch(h);
     };
