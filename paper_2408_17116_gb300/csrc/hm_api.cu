@@ -30,6 +30,31 @@ void dfree(hm_handle_s *h, void *p)
     if (p) cudaFreeAsync(p, h->stream);
 }
 
+void pool_fork(hm_handle_s *h, int n)
+{
+    n = std::min(n, HM_POOL_STREAMS);
+    while ((int)h->pool.size() < n) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        HM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->pool.push_back(s);
+        h->pool_ev.push_back(e);
+    }
+    cudaEvent_t e = h->pool_ev[0];
+    HM_CUDA(cudaEventRecord(e, h->stream));
+    for (int i = 0; i < n; ++i) HM_CUDA(cudaStreamWaitEvent(h->pool[i], e, 0));
+}
+
+void pool_join(hm_handle_s *h, int n)
+{
+    n = std::min(n, HM_POOL_STREAMS);
+    for (int i = 0; i < n; ++i) {
+        HM_CUDA(cudaEventRecord(h->pool_ev[i], h->pool[i]));
+        HM_CUDA(cudaStreamWaitEvent(h->stream, h->pool_ev[i], 0));
+    }
+}
+
 namespace {
 
 struct Timer {
@@ -125,9 +150,8 @@ void free_all(hm_handle_s *h)
     h->d_near = nullptr;
     h->d_perm = h->d_iperm = nullptr;
     h->d_d1 = nullptr;
-    dfree(h, h->tc_ws);
-    h->tc_ws = nullptr;
-    h->tc_ws_bytes = 0;
+    for (auto &w : h->tc_ws) dfree(h, w.p);
+    h->tc_ws.clear();
 }
 
 void collect_leaves(Block *b, std::vector<Block *> &out)
@@ -1127,6 +1151,8 @@ void hm_destroy(hm_handle h)
     }
     for (cudaEvent_t e : h->gemm_free) cudaEventDestroy(e);
     if (h->d_tc_err) cudaFree(h->d_tc_err);
+    for (cudaStream_t ps : h->pool) cudaStreamDestroy(ps);
+    for (cudaEvent_t pe : h->pool_ev) cudaEventDestroy(pe);
     delete h;
 }
 

@@ -482,9 +482,66 @@ static void hlu_rec(hm_handle_s *h, BlockT<Z> *A, int *d_info)
 // triangular solve and every diagonal step flushes its target subtree first), so
 // only low-rank leaves are checked there.  tol: truncation tolerance of every
 // recompression performed by the factorisation.
+// Independent bodies with each body's diagonal block dense: every block above the bodies is
+// hierarchical with zero off-diagonal children, so the H-LU is one dense LU per body.  The
+// diagonal blocks, or false when the tree has another shape.
+template <class Z>
+static bool collect_body_blocks(BlockT<Z> *b, std::vector<BlockT<Z> *> &out)
+{
+    if (b->type == B_DENSE) {
+        out.push_back(b);
+        return true;
+    }
+    if (b->type != B_HIER) return false;
+    for (int i = 1; i <= 2; ++i)
+        if (!(b->ch[i]->type == B_LR && b->ch[i]->k == 0 && b->ch[i]->pend_k == 0)) return false;
+    return collect_body_blocks(b->ch[0], out) && collect_body_blocks(b->ch[3], out);
+}
+
+// The per-body LUs of a batch, concurrently on the stream pool (largest first, round robin).
+template <class Z>
+static bool hlu_factor_bodies(hm_handle_s *h, BlockT<Z> *root)
+{
+    std::vector<BlockT<Z> *> diag;
+    if (!collect_body_blocks(root, diag) || diag.size() < 2) return false;
+    std::stable_sort(diag.begin(), diag.end(), [](const BlockT<Z> *a, const BlockT<Z> *b) { return a->nr > b->nr; });
+    int *d_info = (int *)dalloc(h, sizeof(int));
+    HM_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), h->stream));
+    for (BlockT<Z> *d : diag)
+        if (!d->piv) d->piv = (int *)dalloc(h, sizeof(int) * d->nr);
+    const int ns = (int)std::min<size_t>(HM_POOL_STREAMS, diag.size());
+    h->d_info_cur = d_info;
+    pool_fork(h, ns);
+    cudaStream_t main = h->stream;
+    try {
+        for (size_t i = 0; i < diag.size(); ++i) {
+            h->stream = h->pool[i % ns];
+            zgetrf(h, diag[i]->nr, diag[i]->D, diag[i]->nr, diag[i]->piv, d_info);
+        }
+    } catch (...) {
+        h->stream = main;
+        pool_join(h, ns);
+        h->d_info_cur = nullptr;
+        cudaStreamSynchronize(h->stream);
+        dfree(h, d_info);
+        throw;
+    }
+    h->stream = main;
+    pool_join(h, ns);
+    h->d_info_cur = nullptr;
+    int info = 0;
+    HM_CUDA(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    dfree(h, d_info);
+    if (info < 0) throw HmError{HM_ERR_TIMEOUT, "H-LU: a bounded grid barrier of the panel LU expired"};
+    if (info) throw HmError{HM_ERR_SINGULAR, "H-LU: zero pivot in a diagonal leaf"};
+    return true;
+}
+
 template <class Z>
 void hlu_factor(hm_handle_s *h, BlockT<Z> *root, double tol)
 {
+    if (h->prm.independent && h->dense_lev == HM_MERGE_BODIES && hlu_factor_bodies(h, root)) return;
     double saved = h->cur_tol;
     h->cur_tol = tol;
     int *d_info = (int *)dalloc(h, sizeof(int));

@@ -180,9 +180,17 @@ struct hm_handle_s {
     double phase_s[PH_COUNT] = {0, 0, 0, 0, 0};
     // tensor-core products (hm_tc.cu): packed-operand workspace (grow-only) and the
     // device flag of an expired pipeline wait
-    void *tc_ws = nullptr;
-    size_t tc_ws_bytes = 0;
+    struct TcWs {
+        cudaStream_t s;
+        void *p;
+        size_t bytes;
+    };
+    std::vector<TcWs> tc_ws;  // one grow-only workspace per stream that runs products
     int *d_tc_err = nullptr;
+    // streams for independent work (the LUs of independent bodies, the inverses of the
+    // diagonal tiles): forked from and joined back into `stream` with events
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> pool_ev;
     // block-row plans (hm_tiles.cu): product with the FP64 H-matrix, sweeps of the factors
     TileOp<zc> *tmat64 = nullptr, *tmatcopy = nullptr, *tfac64 = nullptr;
     TileOp<cf> *tfac32 = nullptr;
@@ -267,6 +275,11 @@ template <class C>
 void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std::vector<int> &ranks, double tol);
 
 void phase_collect(hm_handle_s *h);
+// The first n streams of the pool start after the work issued so far on h->stream (fork), and
+// h->stream waits for everything they were given (join).
+void pool_fork(hm_handle_s *h, int n);
+void pool_join(hm_handle_s *h, int n);
+#define HM_POOL_STREAMS 8
 struct PhaseScope {
     hm_handle_s *h;
     int id;

@@ -606,15 +606,23 @@ void tc_gemm(hm_handle_s *h, char opA, char opB, int m, int n, int k, cf alpha, 
     const size_t abytes = (size_t)2 * m * 2 * kp_max * sizeof(__nv_bfloat16);
     const size_t bbytes = (size_t)2 * n * 2 * kp_max * sizeof(__nv_bfloat16);
     const size_t need = ((abytes + 1023) & ~(size_t)1023) + bbytes;
-    if (need > h->tc_ws_bytes) {
-        if (h->tc_ws) dfree(h, h->tc_ws);
-        h->tc_ws = nullptr;
-        h->tc_ws_bytes = 0;
-        h->tc_ws = dalloc(h, need);
-        h->tc_ws_bytes = need;
+    // the packed operands of this stream (products on other streams have their own)
+    hm_handle_s::TcWs *ws = nullptr;
+    for (auto &w : h->tc_ws)
+        if (w.s == h->stream) ws = &w;
+    if (!ws) {
+        h->tc_ws.push_back(hm_handle_s::TcWs{h->stream, nullptr, 0});
+        ws = &h->tc_ws.back();
     }
-    __nv_bfloat16 *pa = (__nv_bfloat16 *)h->tc_ws;
-    __nv_bfloat16 *pb = (__nv_bfloat16 *)((char *)h->tc_ws + ((abytes + 1023) & ~(size_t)1023));
+    if (need > ws->bytes) {
+        if (ws->p) dfree(h, ws->p);
+        ws->p = nullptr;
+        ws->bytes = 0;
+        ws->p = dalloc(h, need);
+        ws->bytes = need;
+    }
+    __nv_bfloat16 *pa = (__nv_bfloat16 *)ws->p;
+    __nv_bfloat16 *pb = (__nv_bfloat16 *)((char *)ws->p + ((abytes + 1023) & ~(size_t)1023));
     const bool ca = opA == 'C', cb = opB == 'C';
     for (int k0 = 0; k0 < k; k0 += TC_KC) {
         const int kc = std::min(TC_KC, k - k0);

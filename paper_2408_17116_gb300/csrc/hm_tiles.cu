@@ -668,14 +668,27 @@ TileOp<C> *tile_build(hm_handle_s *h, BlockT<C> *root, bool factored)
             }
             T->d_inv = (C *)dalloc(h, sizeof(C) * std::max<size_t>(tot, 1));
             T->owned.push_back(T->d_inv);
-            for (int i = 0; i < T->ntile; ++i) {
-                const int n = T->rows[i];
-                BlockT<C> *d = tdiag[i];
-                const size_t o = (size_t)(T->r0[i] - d->r0);
-                const C *Dii = d->D + o + o * d->nr;
-                C *Li = T->d_inv + T->inv_off[i], *Ui = Li + (size_t)n * n;
-                ztri_inverses(h, Dii, d->nr, n, Li, Ui);
+            // the tiles' inverses are independent: concurrently on the stream pool
+            const int ns = std::min(HM_POOL_STREAMS, T->ntile);
+            pool_fork(h, ns);
+            cudaStream_t main = h->stream;
+            try {
+                for (int i = 0; i < T->ntile; ++i) {
+                    h->stream = h->pool[i % ns];
+                    const int n = T->rows[i];
+                    BlockT<C> *d = tdiag[i];
+                    const size_t o = (size_t)(T->r0[i] - d->r0);
+                    const C *Dii = d->D + o + o * d->nr;
+                    C *Li = T->d_inv + T->inv_off[i], *Ui = Li + (size_t)n * n;
+                    ztri_inverses(h, Dii, d->nr, n, Li, Ui);
+                }
+            } catch (...) {
+                h->stream = main;
+                pool_join(h, ns);
+                throw;
             }
+            h->stream = main;
+            pool_join(h, ns);
             // the pivots of each diagonal leaf as one gather: applying the interchanges
             // k <-> piv[k] in order to z is z_new[j] = z_old[g[j]]
             std::vector<int> gall;
