@@ -366,6 +366,13 @@ void hm_destroy(hm_handle h);
 hm_status hm_plan_host(const double *xyz, int nnode, int dof, int leaf, double eta, int *nblocks, int *blocks,
                        int *perm_node);
 
+/* hm_plan_host for a batch of independent bodies (hm_params.independent): node_body
+ * [nnode] gives each node's body, nodes of one body contiguous and bodies in increasing
+ * order.  Clusters are split by bodies first, then bisected geometrically down to `leaf`
+ * unknowns; a block whose clusters share no body is a zero block, reported with type 2. */
+hm_status hm_plan_bodies_host(const double *xyz, const int *node_body, int nnode, int dof, int leaf, double eta,
+                              int *nblocks, int *blocks, int *perm_node);
+
 /* N-Mueller formulation of a dielectric body (Sec. II.A, Eqs. 7-9 with
  * alpha = -eps_r, beta = -1, mu_r = 1): the far (Nystrom) entries of target node tn
  * over every node of source patch p, evaluated on the host with the library's geometry

@@ -296,10 +296,13 @@ void build_cluster_tree(hm_handle_s *h)
     h->clusters[root].body_root = h->prm.independent && h->clusters[root].b0 == h->clusters[root].b1;
 }
 
-extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int leaf, double eta, int *nblocks,
-                                  int *blocks, int *perm_node)
+static hm_status plan_host(const double *xyz, const int *node_body, int nnode, int dof, int leaf, double eta,
+                           int *nblocks, int *blocks, int *perm_node)
 {
     if (!xyz || nnode <= 0 || (dof != 2 && dof != 4) || leaf < dof || !(eta > 0.0) || !nblocks) return HM_ERR_ARG;
+    if (node_body)
+        for (int i = 1; i < nnode; ++i)
+            if (node_body[i] < node_body[i - 1] || node_body[0] < 0) return HM_ERR_ARG;
     try {
         hm_handle_s h;  // host-only planning: no stream, no device memory
         h.nnode = nnode;
@@ -307,6 +310,8 @@ extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int lea
         h.N = dof * nnode;
         h.prm.leaf = leaf;
         h.prm.eta = eta;
+        h.prm.independent = node_body ? 1 : 0;
+        if (node_body) h.node_body.assign(node_body, node_body + nnode);
         h.h_nodes.assign(14 * (size_t)nnode, 0.0);
         for (int i = 0; i < nnode; ++i)
             for (int d = 0; d < 3; ++d) h.h_nodes[(size_t)d * nnode + i] = xyz[3 * (size_t)i + d];
@@ -317,7 +322,7 @@ extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int lea
             for (size_t i = 0; i < h.leaves.size(); ++i) {
                 const Block *b = h.leaves[i];
                 int *o = blocks + 5 * i;
-                o[0] = b->type == B_DENSE ? 0 : 1;
+                o[0] = b->type == B_DENSE ? 0 : (b->zero ? 2 : 1);
                 o[1] = b->r0;
                 o[2] = b->nr;
                 o[3] = b->c0;
@@ -325,10 +330,24 @@ extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int lea
             }
         if (perm_node) std::copy(h.perm_node.begin(), h.perm_node.end(), perm_node);
         for (Block *b : h.blocks) delete b;
+        h.blocks.clear();
         return HM_OK;
     } catch (...) {
         return HM_ERR_OOM;
     }
+}
+
+extern "C" hm_status hm_plan_host(const double *xyz, int nnode, int dof, int leaf, double eta, int *nblocks,
+                                  int *blocks, int *perm_node)
+{
+    return plan_host(xyz, nullptr, nnode, dof, leaf, eta, nblocks, blocks, perm_node);
+}
+
+extern "C" hm_status hm_plan_bodies_host(const double *xyz, const int *node_body, int nnode, int dof, int leaf,
+                                         double eta, int *nblocks, int *blocks, int *perm_node)
+{
+    if (!node_body) return HM_ERR_ARG;
+    return plan_host(xyz, node_body, nnode, dof, leaf, eta, nblocks, blocks, perm_node);
 }
 
 void rebuild_block_tree(hm_handle_s *h)

@@ -36,7 +36,7 @@ EXPORTS = ("hm_version", "hm_create", "hm_build_geometry", "hm_fill", "hm_factor
            "hm_set_rank_model", "hm_mlp_create", "hm_mlp_num_params", "hm_mlp_set_params", "hm_mlp_get_params",
            "hm_mlp_forward", "hm_mlp_loss_grad", "hm_mlp_train", "hm_mlp_last_error", "hm_mlp_destroy",
            "hm_farfield_static", "hm_plan_host", "hm_muller_far_block_host", "hm_muller_near_block_host",
-           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host", "hm_cgemm", "hm_tc_tuning")
+           "hm_muller_rhs_farfield_host", "hm_inject_fault", "hm_get_trunc_log_host", "hm_cgemm", "hm_tc_tuning", "hm_plan_bodies_host")
 
 
 class hm_params(ctypes.Structure):
@@ -85,6 +85,7 @@ def load(path=SO):
     L.hm_matvec.argtypes = [P, I, P, P]
     L.hm_farfield_static.argtypes = [P, I, P, I, P, P, P]
     L.hm_plan_host.argtypes = [P, I, I, I, D, ctypes.POINTER(I), P, P]
+    L.hm_plan_bodies_host.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P, P]
     L.hm_muller_far_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, P]
     L.hm_muller_near_block_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, D, D, I, I, I, I, I, D, P]
     L.hm_muller_rhs_farfield_host.argtypes = [ctypes.POINTER(hm_body), I, I, D, P, P, P, P, I, P, P]
@@ -140,6 +141,25 @@ def plan_host(xyz, leaf, eta, dof=2):
                         _np_ptr(blocks), _np_ptr(perm))
     if st != HM_OK:
         raise HmError(st, "hm_plan_host")
+    return blocks, perm
+
+
+def plan_bodies_host(xyz, node_body, leaf, eta, dof=2):
+    """hm_plan_bodies_host (host only): the block cluster tree of a batch of independent
+    bodies, (blocks [n][5] with type 2 for zero blocks between bodies, perm_node [nnode])."""
+    L = load()
+    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    nb = np.ascontiguousarray(np.asarray(node_body, dtype=np.int32))
+    n = ctypes.c_int()
+    args = (_np_ptr(xyz), _np_ptr(nb), xyz.shape[0], int(dof), int(leaf), float(eta), ctypes.byref(n))
+    st = L.hm_plan_bodies_host(*args, None, None)
+    if st != HM_OK:
+        raise HmError(st, "hm_plan_bodies_host")
+    blocks = np.empty((n.value, 5), dtype=np.int32)
+    perm = np.empty(xyz.shape[0], dtype=np.int32)
+    st = L.hm_plan_bodies_host(*args, _np_ptr(blocks), _np_ptr(perm))
+    if st != HM_OK:
+        raise HmError(st, "hm_plan_bodies_host")
     return blocks, perm
 
 

@@ -90,3 +90,43 @@ def test_collinear_points_split_along_the_line():
     # bisection along x keeps the order of the line (up to the tie rule)
     assert np.array_equal(perm, np.arange(200))
     assert (blocks[:, 0] == 1).any()
+
+
+@pytest.mark.parametrize("dof", [2, 4])
+def test_batch_planner_separates_bodies(dof):
+    # a batch of independent bodies (hm_plan_bodies_host): the leaves still tile the matrix
+    # exactly once; a block whose rows and columns lie on different bodies is a zero block
+    # (type 2) and every other leaf lies on one body; clusters hold at most n_leaf unknowns
+    wl = workloads.workload("batch_spheroids3")
+    o = oracle.Oracle(wl["bodies"], wl["ms"], wl["nc"], wl["k"])
+    xyz = o.node_table()[:, :3]
+    sizes = [6 * m * m * wl["nc"] ** 2 for m in wl["ms"]]
+    node_body = np.repeat(np.arange(len(sizes)), sizes)
+    assert node_body.size == xyz.shape[0]
+    blocks, perm = hm.plan_bodies_host(xyz, node_body, wl["leaf"], wl["eta"], dof)
+    n = xyz.shape[0]
+    N = dof * n
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    tree_body = np.repeat(node_body[perm], dof)  # body of each tree-ordered unknown
+    cover = np.zeros((N, N), dtype=np.int16)
+    zero = 0
+    for typ, r0, nr, c0, nc in blocks:
+        cover[r0:r0 + nr, c0:c0 + nc] += 1
+        rb, cb = np.unique(tree_body[r0:r0 + nr]), np.unique(tree_body[c0:c0 + nc])
+        if np.intersect1d(rb, cb).size == 0:
+            assert typ == 2
+            zero += 1
+        else:
+            assert typ in (0, 1) and len(rb) == 1 and len(cb) == 1 and rb[0] == cb[0]
+            if typ == 0:
+                assert nr <= wl["leaf"] or nc <= wl["leaf"]
+    assert np.all(cover == 1)
+    assert zero >= len(sizes) - 1
+    # the nodes of each body stay together in tree order
+    assert np.all(np.diff(node_body[perm]) >= 0)
+
+
+def test_batch_planner_rejects_unsorted_bodies():
+    xyz = np.random.default_rng(0).standard_normal((40, 3))
+    with pytest.raises(hm.HmError):
+        hm.plan_bodies_host(xyz, np.array([1] * 20 + [0] * 20), 8, 2.0)
