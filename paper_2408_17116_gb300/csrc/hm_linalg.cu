@@ -730,7 +730,7 @@ template <class C>
 void zcopy2d(hm_handle_s *h, MVT<C> dst, MVT<C> src);
 
 #define LU_NB 32    // columns of a panel step (one CTA)
-#define LU_NBO 256  // columns of an outer step: its trailing update is a product of depth 256
+#define LU_NBO 512  // columns of an outer step: its trailing update is a product of depth 512
 
 template <class C>
 void zgetrf(hm_handle_s *h, int n, C *A, int lda, int *piv, int *d_info)
