@@ -3,6 +3,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2408_17116_gb300 import build, hm
@@ -89,3 +90,10 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
         assert int(out[st]) == ctypes.sizeof(cls), st
         for f in fields[st]:
             assert int(out["%s.%s" % (st, f)]) == getattr(cls, f).offset, (st, f)
+
+
+def test_tensor_core_tuning_record_is_readable_without_a_gpu():
+    # the autotuner's record is host state: readable (all classes untuned) before any product
+    st, ms = hm.tc_tuning()
+    assert st.shape == (8,) and ms.shape == (8, 3)
+    assert set(np.unique(st)).issubset({0, 1, 2, 4})
