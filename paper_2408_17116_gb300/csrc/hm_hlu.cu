@@ -1,6 +1,8 @@
-// H-LU factorisation and H-solve (Sec. III and III.A: block LU of Eq. 23 applied
-// recursively, forward substitution Eqs. 24, 26, 27, back substitution Eqs. 25,
-// 28), on the entire-matrix block cluster tree (Sec. III.B: one tree over all unknowns).
+// H-LU factorisation (Sec. III: block LU of Eq. 23 applied recursively) on the
+// entire-matrix block cluster tree (Sec. III.B: one tree over all unknowns).  The
+// substitutions of Eqs. 24-28 with the factors run as block-row sweeps (hm_tiles.cu); the
+// H-triangular solves below serve the factorisation itself (L^-1 and U^-1 applied to the
+// off-diagonal blocks).
 //
 // Recursion on a diagonal block A = [[A11, A12], [A21, A22]]:
 //   A11 = P1^T L11 U11                       (recursive; partial pivoting inside dense leaves)
@@ -15,7 +17,6 @@
 #include <algorithm>
 
 #include "hm_internal.h"
-
 
 template <class Z>
 static inline MVT<Z> rows_of(MVT<Z> X, int r0, int nr) { return MVT<Z>{X.p + r0, nr, X.cols, X.ld}; }
@@ -567,13 +568,6 @@ void hlu_factor(hm_handle_s *h, BlockT<Z> *root, double tol)
     if (info) throw HmError{HM_ERR_SINGULAR, "H-LU: zero pivot in a diagonal leaf"};
 }
 
-template <class Z>
-void hsolve(hm_handle_s *h, BlockT<Z> *root, MVT<Z> X)
-{
-    trsm_L_mv(h, root, X);
-    trsm_U_mv(h, root, X);
-}
-
 template <class Ti, class To>
 __global__ void k_convert(const Ti *__restrict__ x, To *__restrict__ y, size_t n)
 {
@@ -910,7 +904,6 @@ int dense_level_by_memory(hm_handle_s *h, BlockT<Z> *root, double budget_words)
 
 #define HM_INST_HLU(Z)                                                                             \
     template void hlu_factor<Z>(hm_handle_s *, BlockT<Z> *, double);                               \
-    template void hsolve<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>);                                   \
     template void hmatvec<Z>(hm_handle_s *, BlockT<Z> *, MVT<Z>, MVT<Z>, Z, bool);                 \
     template BlockT<Z> *clone_tree<Z>(hm_handle_s *, Block *, std::vector<BlockT<Z> *> &);         \
     template void free_tree<Z>(hm_handle_s *, std::vector<BlockT<Z> *> &);                         \

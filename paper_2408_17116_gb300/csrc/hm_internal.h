@@ -266,11 +266,6 @@ struct QRJob {
 };
 template <class C>
 void batched_qr(hm_handle_s *h, const std::vector<QRJob<C>> &jobs);
-// Truncated recompression of A = U V^H (U m x K, V n x K): returns the new rank;
-// *Uo, *Vo receive freshly allocated factors (balanced: both scaled by sqrt(sigma)).
-template <class C>
-int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const C *V, int ldv, double tol, int kmax,
-                C **Uo, C **Vo);
 template <class C>
 void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std::vector<int> &ranks, double tol);
 
@@ -322,8 +317,6 @@ void launch_farfield(hm_handle_s *h, int nrhs, const zc *d_x, int nang, const do
 // ---- hm_hlu.cu (instantiated for complex128 and complex64) ----
 template <class C>
 void hlu_factor(hm_handle_s *h, BlockT<C> *root, double tol);
-template <class C>
-void hsolve(hm_handle_s *h, BlockT<C> *root, MVT<C> X);  // X (tree order) <- A^-1 X
 template <class C>
 void hmatvec(hm_handle_s *h, BlockT<C> *A, MVT<C> X, MVT<C> Y, C alpha, bool conjtrans);  // Y += alpha op(A) X
 // Deep copy of a block tree, converting the storage precision (complex128 -> C).

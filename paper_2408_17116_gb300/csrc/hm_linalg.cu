@@ -1732,34 +1732,6 @@ static void fetch_sv(hm_handle_s *h, std::vector<TruncJob<C>> &jobs, std::vector
     for (size_t i = 0; i < jobs.size(); ++i) S[i].assign(Sr[i].begin(), Sr[i].end());
 }
 
-template <class C>
-int truncate_lr(hm_handle_s *h, int m, int n, int K, const C *U, int ldu, const C *V, int ldv, double tol, int kmax,
-                C **Uo, C **Vo)
-{
-    *Uo = *Vo = nullptr;
-    if (K <= 0 || m <= 0 || n <= 0) return 0;
-    std::vector<TruncJob<C>> jobs(1);
-    jobs[0] = TruncJob<C>{};
-    jobs[0].m = m;
-    jobs[0].n = n;
-    jobs[0].K = K;
-    jobs[0].U = U;
-    jobs[0].ldu = ldu;
-    jobs[0].V = V;
-    jobs[0].ldv = ldv;
-    jobs[0].kmax = kmax;
-    double saved = h->cur_tol;
-    h->cur_tol = tol;
-    trunc_stage1(h, jobs);
-    h->cur_tol = saved;
-    std::vector<std::vector<double>> S;
-    std::vector<std::vector<int>> ord;
-    fetch_sv(h, jobs, S, ord);
-    account_kernels(h);
-    if (use_qrcp<C>(h)) h->kcore_flops += householder_flops(jobs[0].r1, jobs[0].r2, ord[0][0]);
-    if (use_qrcp<C>(h)) return trunc_stage2_qrcp(h, jobs[0], std::min(ord[0][0], kmax > 0 ? kmax : K), Uo, Vo);
-    return trunc_stage2(h, jobs[0], S[0], ord[0], tol, Uo, Vo);
-}
 
 // Recompress the low-rank leaves blks (U, V with ranks[i] columns) in one batch;
 // replaces b->U, b->V, b->k.
@@ -1843,7 +1815,6 @@ void batched_truncate(hm_handle_s *h, std::vector<BlockT<C> *> &blks, const std:
     template void ztri_inverses<C>(hm_handle_s *, const C *, int, int, C *, C *);                                 \
     template void zcopy2d<C>(hm_handle_s *, MVT<C>, MVT<C>);                                                      \
     template void zscale_cols<C>(hm_handle_s *, MVT<C>, const typename CReal<C>::R *);                            \
-    template int truncate_lr<C>(hm_handle_s *, int, int, int, const C *, int, const C *, int, double, int, C **, C **); \
     template void batched_truncate<C>(hm_handle_s *, std::vector<BlockT<C> *> &, const std::vector<int> &, double);
 HM_INST_LINALG(zc)
 HM_INST_LINALG(cf)
