@@ -55,3 +55,22 @@ def test_single_process_aggregate():
     import bench
     ms, value = bench.aggregate(250.0, 500, None)
     assert ms == 250.0 and abs(value - 2000.0) < 1e-12
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm (the oracle on the host cores) prints one JSON line with the keys the
+    # bench contract names, on the same workload description as the native arm
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "sphere_d1_m1_nc8", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["workload"] == "sphere_d1_m1_nc8" and line["config"]["unknowns"] == 768
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
