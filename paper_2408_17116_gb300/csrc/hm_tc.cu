@@ -534,7 +534,12 @@ static int tc_stages(hm_handle_s *h, const CUtensorMap &ma, const CUtensorMap &m
     const int dflt = kp <= 512 ? 2 : 4;
     if (m < 2048 || n < 2048) return dflt;
     const int ms = m, ns = (int)std::min<long long>(n, std::max<long long>(256, (1LL << 28) / m));
-    cf *scratch = (cf *)dalloc(h, sizeof(cf) * (size_t)ms * ns);
+    cf *scratch = nullptr;
+    try {
+        scratch = (cf *)dalloc(h, sizeof(cf) * (size_t)ms * ns);
+    } catch (const HmError &) {
+        return dflt;  // no room for the timing block: the default variant, tuned later
+    }
     const dim3 grid((2 * ms + TC_BM - 1) / TC_BM, (2 * ns + TC_BN - 1) / TC_BN);
     cudaEvent_t e0 = gemm_event(h), e1 = gemm_event(h);
     float best[3] = {1e30f, 1e30f, 1e30f};
